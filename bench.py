@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Benchmark: SHA3-256 over 2^24 messages of 64 bytes on one GB300 (Mhash/s).
+
+One step = one call of keccak_batch_uniform (the fixed-stride batch mode of
+the paper's Section 4: one thread per message, same-length messages) over
+2^24 seeded random 64-byte messages already resident in HBM.  The inputs
+(1 GiB) are larger than L2, so no flush is needed between steps.
+
+Printed (rank 0, one JSON line): the headline Mhash/s, the ALU roofline of the
+hashing kernel, an end-to-end figure through keccak_batch_uniform_host (host
+buffers, copies inside the timed region), SM clocks sampled during the timed
+region, and the CPU oracle timed on a bounded sample of the same messages.
+
+``--impl reference`` times the CPU oracle alone on the same workload and
+metric (there is no other implementation of the paper's method to run).
+
+Multi-GPU (torchrun): every rank hashes its own 2^24 messages (weak scaling,
+no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_MSGS = 1 << 24
+MSG_BYTES = 64
+DIGEST = 32
+VARIANT = 1  # SHA3-256
+WORKLOAD = "sha3_256_2p24_msgs_x_64B"
+METRIC = "SHA3-256 Mhash/s (64 B msgs)"
+
+# Algorithmic 32-bit integer operations of one Keccak-f[1600] permutation in
+# the bit-interleaved form: per round theta 20 (parities) + 5 (rotate) + 50
+# (apply), rho 47, chi 50, plus iota's non-zero halves (derived below).
+ROUND_OPS_NO_IOTA = 20 + 5 + 50 + 47 + 50
+
+# SMs x 32-bit integer lanes per SM per clock x maximum SM clock: the ALU
+# issue roofline (see the design doc for the derivation and the probe that
+# confirms the lane count).
+SM_COUNT_GB300 = 152
+INT_LANES_PER_SM_CLK = 128
+SM_MAX_MHZ = 2070.0
+
+
+def _interleaved_nonzero_halves() -> int:
+    """Number of non-zero 32-bit halves among the 24 round constants."""
+    from paper_1902_05320_gb300 import binding
+
+    total = 0
+    for rc in binding.round_constants():
+        e = sum(((rc >> (2 * k)) & 1) << k for k in range(32))
+        o = sum(((rc >> (2 * k + 1)) & 1) << k for k in range(32))
+        total += (e != 0) + (o != 0)
+    return total
+
+
+def ops_per_permutation() -> int:
+    return 24 * ROUND_OPS_NO_IOTA + _interleaved_nonzero_halves()
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.device_index = device_index
+        self.samples = []
+        self.proc = None
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.device_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.monotonic(), line.strip()))
+
+    def mark(self):
+        self.marks.append(time.monotonic())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        t0, t1 = (self.marks + [0, 0])[:2] if len(self.marks) >= 2 else (0, 1e30)
+        inside = [s for t, s in self.samples if t0 - 0.15 <= t <= t1 + 0.15] or [s for _, s in self.samples]
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for s in inside:
+            parts = [p.strip() for p in s.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(msgs: np.ndarray, seconds: float = 8.0) -> dict:
+    """The CPU oracle, as it stands, on a bounded sample of the messages."""
+    import oracle
+
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+
+    def run(k):
+        offs = np.arange(k, dtype=np.uint64) * np.uint64(MSG_BYTES)
+        t = time.perf_counter()
+        oracle.hash_batch(msgs[: k * MSG_BYTES], offs, np.full(k, MSG_BYTES, np.uint64),
+                          np.full(k, VARIANT, np.uint8), np.full(k, DIGEST, np.uint32), cores)
+        return time.perf_counter() - t
+
+    k0 = 64 * cores
+    dt0 = run(k0)
+    k = int(min(N_MSGS, max(k0, k0 * seconds / max(dt0, 1e-6))))
+    dt = run(k)
+    return {"value": k / dt / 1e6, "unit": "Mhash/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {k} of the 2^24 64-byte messages, SHA3-256, {dt:.1f} s on {cores} host threads"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1902_05320_gb300 import workloads
+
+    import oracle
+
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    msgs = workloads.uniform_messages(N_MSGS, MSG_BYTES, seed=1)
+    # Each step hashes a bounded sample sized so the whole run takes ~2 minutes.
+    probe = 64 * cores
+    offs = np.arange(probe, dtype=np.uint64) * np.uint64(MSG_BYTES)
+    t = time.perf_counter()
+    oracle.hash_batch(msgs[: probe * MSG_BYTES], offs, np.full(probe, MSG_BYTES, np.uint64),
+                      np.full(probe, VARIANT, np.uint8), np.full(probe, DIGEST, np.uint32), cores)
+    rate = probe / (time.perf_counter() - t)
+    per_step = int(max(probe, min(N_MSGS, rate * 100.0 / max(1, args.steps + args.warmup))))
+    offs = np.arange(per_step, dtype=np.uint64) * np.uint64(MSG_BYTES)
+    lens = np.full(per_step, MSG_BYTES, np.uint64)
+    var = np.full(per_step, VARIANT, np.uint8)
+    ol = np.full(per_step, DIGEST, np.uint32)
+    sample = msgs[: per_step * MSG_BYTES]
+    for _ in range(args.warmup):
+        oracle.hash_batch(sample, offs, lens, var, ol, cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.hash_batch(sample, offs, lens, var, ol, cores)
+    dt = (time.perf_counter() - t) / max(1, args.steps)
+    value = per_step / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mhash/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step": per_step,
+                   "note": "CPU oracle (bit-level FIPS 202 restatement) on host cores; bounded sample per step"},
+        "cpu_baseline": {"value": value, "unit": "Mhash/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {per_step} of the 2^24 64-byte messages per step"},
+        "e2e": {"value": value, "unit": "Mhash/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1902_05320_gb300 import binding, build, workloads
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    binding.load()
+
+    msgs_np = workloads.uniform_messages(N_MSGS, MSG_BYTES, seed=1 + rank)
+    msgs = torch.from_numpy(msgs_np).cuda()
+    digests = torch.empty(N_MSGS * DIGEST, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        binding.keccak_batch_uniform(msgs, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, digests, N_MSGS, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # Spot check before timing: a few digests against hashlib.
+    got = digests[: 4 * DIGEST].cpu().numpy().reshape(4, DIGEST)
+    for i in range(4):
+        want = hashlib.sha3_256(msgs_np[i * MSG_BYTES:(i + 1) * MSG_BYTES].tobytes()).digest()
+        if got[i].tobytes() != want:
+            raise SystemExit(f"digest mismatch at message {i}")
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark()
+    start.record(stream)
+    for _ in range(args.steps):
+        step()
+    end.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark()
+    if world > 1:
+        dist.barrier()
+    ms = start.elapsed_time(end) / args.steps
+    time.sleep(0.2)
+    sampler.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = sampler.summary()
+
+    value = world * N_MSGS / (ms / 1e3) / 1e6
+    ops_perm = ops_per_permutation()
+    achieved = N_MSGS * ops_perm / (ms / 1e3) / 1e12
+    peak = SM_COUNT_GB300 * INT_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = measured_traffic()
+
+    # End to end through the host-buffer entry point (copies in the timed region).
+    h_in = torch.from_numpy(msgs_np).pin_memory()
+    h_out = torch.empty(N_MSGS * DIGEST, dtype=torch.uint8).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, N_MSGS, stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, N_MSGS, stream)
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    if not torch.equal(h_out[: 1 << 20], digests[: 1 << 20].cpu()):
+        raise SystemExit("host-buffer path disagrees with the device path")
+    e2e_value = world * N_MSGS / e2e_s / 1e6
+
+    extra = {} if args.no_extra else extra_measurements(binding, workloads, torch, stream, msgs, rank)
+    del msgs, digests
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mhash/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "messages_per_gpu": N_MSGS, "msg_bytes": MSG_BYTES,
+                   "variant": "SHA3-256", "entry_point": "keccak_batch_uniform",
+                   "l2": "inputs (1 GiB per step) larger than L2; no flush", "parallelism": f"replicas{world}"},
+        "gb_per_s": world * N_MSGS * MSG_BYTES / (ms / 1e3) / 1e9,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "ops_per_hash": ops_perm,
+                     "peak_basis": f"{SM_COUNT_GB300} SMs x {INT_LANES_PER_SM_CLK} int32 lanes/clk x "
+                                   f"{SM_MAX_MHZ:.0f} MHz max SM clock",
+                     "kernel": "k_sha3_uniform<SHA3-256, 64 B>"},
+        "e2e": {"value": e2e_value, "unit": "Mhash/s", "h2d_bytes_per_step": N_MSGS * MSG_BYTES,
+                "d2h_bytes_per_step": N_MSGS * DIGEST, "entry_point": "keccak_batch_uniform_host (pinned)"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if extra:
+        line["extra"] = extra
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(msgs_np)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def extra_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
+    """Secondary figures of the same fixed-length batch family (not the headline)."""
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    d64 = torch.empty(N_MSGS * 64, dtype=torch.uint8, device="cuda")
+    ms = timed(lambda: binding.keccak_batch_uniform(msgs, 64, 64, 3, 64, d64, N_MSGS, stream))
+    out["sha3_512_2p24_x_64B_mhash_s"] = N_MSGS / ms / 1e3
+    del d64
+    n2, l2 = 1 << 22, 1024
+    m2 = torch.from_numpy(workloads.uniform_messages(n2, l2, seed=2 + rank)).cuda()
+    d2 = torch.empty(n2 * 32, dtype=torch.uint8, device="cuda")
+    ms = timed(lambda: binding.keccak_batch_uniform(m2, l2, l2, 1, 32, d2, n2, stream))
+    out["sha3_256_2p22_x_1KiB_mhash_s"] = n2 / ms / 1e3
+    out["sha3_256_2p22_x_1KiB_gb_s"] = n2 * l2 / ms / 1e6
+    del m2, d2
+    try:
+        out["int_lanes_per_sm_clk"] = {name: round(binding.int_issue_probe(op, 4096, stream), 2)
+                                       for op, name in enumerate(("lop3", "shf", "prmt", "iadd"))}
+    except Exception as e:  # diagnostic only
+        out["int_lanes_per_sm_clk"] = f"probe failed: {e}"
+    return out
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the hashing kernel from the committed ncu
+    summary, or None when the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "k_sha3_uniform_sha3_256_64B.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for ln in open(path):
+        if ":" in ln and ln.startswith("- "):
+            k, v = ln[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    try:
+        bytes_per_launch = float(fields["dram_bytes_per_launch_full_size"])
+        recorded = fields["csrc_sha256"]
+    except (KeyError, ValueError):
+        return None
+    return bytes_per_launch if recorded == csrc_digest() else None
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1902_05320_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")) and name in ("keccak_core.cuh", "sponge.cuh", "sha3_uniform.cu",
+                                                       "runtime.cuh"):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * sha3gb.h -- C ABI of the batch SHA-3 library for NVIDIA GB300 (sm_103a).
+ *
+ * The library hashes many independent messages at once: the batch mode of
+ * Section 4 of "GPU Accelerated Keccak (SHA3) Algorithm" (Wang & Chu), with
+ * one Keccak[c] sponge per message (Section 3.2, Eq. 12) for the six
+ * functions of Eq. 13-18, bit-exact to FIPS 202.  Tree mode (Section 4, named
+ * there as future work) is offered as a binary Merkle root.
+ *
+ * Conventions for every entry point below:
+ *  - Unless marked "host", pointer arguments are CUDA device pointers
+ *    (memory on the current device, e.g. allocated by PyTorch).  The caller
+ *    owns them; the library never frees them.
+ *  - `stream` is a cudaStream_t handle passed as void*; NULL means the legacy
+ *    default stream.  Calls are stream-ordered and return once the work is
+ *    enqueued, unless stated otherwise.
+ *  - Return value: KB_OK (0) or a negative kb_status.  Argument errors are
+ *    detected on the host and returned at once, before anything is enqueued.
+ *  - Byte order: messages and digests are byte strings as in FIPS 202
+ *    Appendix B (bits LSB-first inside each byte).  Only whole-byte messages
+ *    are accepted.
+ *  - Scratch: the library may allocate internal device scratch on first use
+ *    and cache it per device; keccak_release() frees it.
+ */
+#ifndef SHA3GB_H
+#define SHA3GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Variant numbers (Eq. 13-18).  Rate r = 1600 - c bits:
+ *   0 SHA3-224  c=448   r=144 B  digest 28 B
+ *   1 SHA3-256  c=512   r=136 B  digest 32 B
+ *   2 SHA3-384  c=768   r=104 B  digest 48 B
+ *   3 SHA3-512  c=1024  r=72 B   digest 64 B
+ *   4 SHAKE128  c=256   r=168 B  any output length
+ *   5 SHAKE256  c=512   r=136 B  any output length */
+typedef enum {
+    KB_SHA3_224 = 0,
+    KB_SHA3_256 = 1,
+    KB_SHA3_384 = 2,
+    KB_SHA3_512 = 3,
+    KB_SHAKE128 = 4,
+    KB_SHAKE256 = 5
+} kb_variant;
+
+typedef enum {
+    KB_OK = 0,
+    KB_ERR_INVALID = -1,  /* bad argument (null pointer, unknown variant, bad size) */
+    KB_ERR_NOMEM = -2,    /* internal scratch could not be allocated */
+    KB_ERR_CUDA = -3,     /* a CUDA runtime call failed (launch, copy, ...) */
+    KB_ERR_TIMEOUT = -4   /* a bounded device-side wait gave up */
+} kb_status;
+
+/* Bits of the device status word read by keccak_last_error(). */
+#define KB_DEV_BAD_VARIANT 0x1u   /* a message named a variant outside 0..5 */
+#define KB_DEV_BAD_OUTLEN 0x2u    /* a SHA3-x message asked for out_len != digest size */
+#define KB_DEV_TIMEOUT 0x4u       /* a bounded device wait expired */
+
+/*
+ * keccak_batch_uniform -- the fixed-stride batch mode (Section 4, "Batch mode
+ * ... divide a piece of information into multiple identical slices"; Section
+ * 4.3 hashes many same-length messages): message i is the `len` bytes at
+ * msgs + i*stride, i = 0..n-1, all hashed with one variant.  Output i is
+ * `out_len` bytes at digests + i*out_len.
+ *   msgs     device, >= (n-1)*stride + len bytes (may be NULL when len == 0)
+ *   stride   distance in bytes between message starts (any value)
+ *   len      message length in bytes (same for all messages)
+ *   variant  0..5 (kb_variant)
+ *   out_len  digest size for variants 0..3 (28/32/48/64, anything else is
+ *            KB_ERR_INVALID); any value >= 0 for SHAKE
+ *   digests  device, n*out_len bytes
+ * n == 0 is a no-op returning KB_OK.  Reads touch only the 8-byte-aligned
+ * words that hold message bytes.
+ */
+int keccak_batch_uniform(const uint8_t *msgs, uint64_t stride, uint64_t len, int variant,
+                         uint32_t out_len, uint8_t *digests, uint64_t n, void *stream);
+
+/*
+ * keccak_batch -- the ragged batch mode: n independent messages of any
+ * lengths and any mix of the six variants in one call (Section 4 batch mode,
+ * generalised from the paper's equal-length messages of Section 4.3).
+ *   msgs      device byte buffer holding all messages
+ *   offsets   device uint64[n]: message i starts at msgs + offsets[i]
+ *   lens      device uint64[n]: length of message i in bytes
+ *   variant   device uint8[n]: kb_variant of message i
+ *   out_lens  device uint32[n]: output bytes of message i (must equal the
+ *             digest size for variants 0..3)
+ *   digests   device: output i is written at byte exclusive_scan(out_lens)[i]
+ *             (outputs packed back to back in message order)
+ *   n         number of messages; 0 is a no-op
+ * Per-message errors (a variant outside 0..5, a SHA3-x out_len that is not
+ * the digest size) cannot be seen on the host without a sync: those messages
+ * are skipped (their output bytes are left untouched) and a bit is set in the
+ * device status word (see keccak_last_error).  Uses cached internal scratch
+ * of 8 bytes per message plus a small work-queue descriptor.
+ */
+int keccak_batch(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                 const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests,
+                 uint64_t n, void *stream);
+
+/*
+ * keccak_batch_uniform_host -- keccak_batch_uniform on HOST buffers, the whole
+ * job: host-to-device copy of the messages, hashing, device-to-host copy of
+ * the digests, pipelined in chunks over internal streams so copies overlap
+ * with hashing.  Synchronous: returns when h_digests holds every output.
+ *   h_msgs     host, (n-1)*stride + len bytes; page-locked memory gives full
+ *              copy bandwidth, pageable memory works but is slower
+ *   h_digests  host, n*out_len bytes
+ * Other arguments as keccak_batch_uniform.  `stream` orders the job after
+ * earlier work on that stream.  Uses cached device staging buffers.
+ */
+int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t len, int variant,
+                              uint32_t out_len, uint8_t *h_digests, uint64_t n, void *stream);
+
+/*
+ * merkle_sha3_256 -- tree mode (Section 4: messages "hashed in twos until the
+ * Hash Root").  The buffer holds n_leaves leaves of leaf_bytes bytes each;
+ * leaf digest = SHA3-256(0x00 || leaf), node digest = SHA3-256(0x01 || left
+ * || right), level by level, an odd last node carried up unchanged.
+ *   buf        device, n_leaves*leaf_bytes bytes
+ *   root       HOST, 32 bytes, written before the call returns
+ * Synchronous on `stream`.  n_leaves == 0 or leaf_bytes == 0 is
+ * KB_ERR_INVALID; n_leaves == 1 gives the single leaf digest.  Uses cached
+ * scratch of 32 bytes per leaf.
+ */
+int merkle_sha3_256(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *root,
+                    void *stream);
+
+/* Number of nodes in the tree of n_leaves leaves, all levels counted (0 for 0). */
+uint64_t merkle_node_count(uint64_t n_leaves);
+
+/*
+ * merkle_sha3_256_levels -- the same tree, every level kept: nodes (device,
+ * 32*merkle_node_count(n_leaves) bytes) receives the leaf digests, then each
+ * level above, the root last.  Stream-ordered (asynchronous).
+ */
+int merkle_sha3_256_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes,
+                           uint8_t *nodes, void *stream);
+
+/* Synchronises `stream`, returns the device status word (KB_DEV_* bits, 0 if
+ * clean) accumulated by kernels on this device since the last call, and
+ * clears it.  Returns KB_ERR_CUDA if the synchronisation fails. */
+int keccak_last_error(void *stream);
+
+/* Frees the cached scratch, staging buffers, streams and graphs of the
+ * calling thread's current device.  Safe to call at any time when no work
+ * of this library is in flight. */
+void keccak_release(void);
+
+/* The 24 round constants (Definition 5, Eq. 8-9) and 25 rho offsets (lane
+ * index x+5y) compiled into the kernels, written to HOST arrays, so that
+ * tests can compare them with an independent generation. */
+int sha3gb_round_constants(uint64_t *rc24);
+int sha3gb_rho_offsets(uint32_t *rho25);
+
+/* Integer-issue microbenchmark for the ALU roofline (diagnostic, not part of
+ * the hashing path): runs `iters` x 8 dependent-chain instructions per thread
+ * of one kind (op 0 LOP3, 1 SHF funnel rotate, 2 PRMT, 3 32-bit add) on a
+ * one-wave grid and writes the measured thread-instructions issued per SM
+ * clock to *lanes_per_clk_per_sm (HOST).  Synchronous on `stream`; allocates
+ * and frees a small device buffer. */
+int sha3gb_int_issue_probe(int op, uint32_t iters, double *lanes_per_clk_per_sm, void *stream);
+
+/* Library version string (static storage). */
+const char *sha3gb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,175 @@
+"""ctypes binding of ``libsha3gb.so`` (the C ABI of ``include/sha3gb.h``).
+
+Argument marshalling only: every step of the hashing path runs in the CUDA
+library.  Device buffers are passed as torch CUDA tensors (or raw integer
+addresses), host buffers as numpy arrays or torch CPU tensors; ``stream``
+defaults to torch's current stream.  There is no CPU fallback: if the library
+has not been built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsha3gb.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "sha3gb.h")
+
+KB_OK, KB_ERR_INVALID, KB_ERR_NOMEM, KB_ERR_CUDA, KB_ERR_TIMEOUT = 0, -1, -2, -3, -4
+KB_DEV_BAD_VARIANT, KB_DEV_BAD_OUTLEN, KB_DEV_TIMEOUT = 0x1, 0x2, 0x4
+DIGEST_BYTES = (28, 32, 48, 64, None, None)
+RATE_BYTES = (144, 136, 104, 72, 168, 136)
+NAMES = ("SHA3-224", "SHA3-256", "SHA3-384", "SHA3-512", "SHAKE128", "SHAKE256")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class Sha3gbError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what} failed with status {status}")
+        self.status = status
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/sha3gb.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("defined",)))
+
+
+_SIGS = {
+    "keccak_batch_uniform": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                            ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "keccak_batch": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_uint64, ctypes.c_void_p]),
+    "keccak_batch_uniform_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                                 ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
+                                                 ctypes.c_void_p]),
+    "merkle_sha3_256": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "merkle_node_count": (ctypes.c_uint64, [ctypes.c_uint64]),
+    "merkle_sha3_256_levels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                                              ctypes.c_void_p]),
+    "keccak_last_error": (ctypes.c_int, [ctypes.c_void_p]),
+    "keccak_release": (None, []),
+    "sha3gb_round_constants": (ctypes.c_int, [ctypes.c_void_p]),
+    "sha3gb_rho_offsets": (ctypes.c_int, [ctypes.c_void_p]),
+    "sha3gb_version": (ctypes.c_char_p, []),
+    "sha3gb_int_issue_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def load() -> ctypes.CDLL:
+    """Loads the library (built by ``paper_1902_05320_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with `python -m paper_1902_05320_gb300.build` "
+                    "(there is no CPU fallback)")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x).__name__}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int, what: str) -> int:
+    if status < 0:
+        raise Sha3gbError(status, what)
+    return status
+
+
+def keccak_batch_uniform(msgs, stride: int, length: int, variant: int, out_len: int, digests, n: int,
+                         stream=None) -> None:
+    _check(load().keccak_batch_uniform(_ptr(msgs), stride, length, variant, out_len, _ptr(digests), n,
+                                       _stream(stream)), "keccak_batch_uniform")
+
+
+def keccak_batch(msgs, offsets, lens, variants, out_lens, digests, n: int, stream=None) -> None:
+    _check(load().keccak_batch(_ptr(msgs), _ptr(offsets), _ptr(lens), _ptr(variants), _ptr(out_lens),
+                               _ptr(digests), n, _stream(stream)), "keccak_batch")
+
+
+def keccak_batch_uniform_host(h_msgs, stride: int, length: int, variant: int, out_len: int, h_digests,
+                              n: int, stream=None) -> None:
+    _check(load().keccak_batch_uniform_host(_ptr(h_msgs), stride, length, variant, out_len, _ptr(h_digests),
+                                            n, _stream(stream)), "keccak_batch_uniform_host")
+
+
+def merkle_sha3_256(buf, n_leaves: int, leaf_bytes: int, stream=None) -> bytes:
+    root = (ctypes.c_uint8 * 32)()
+    _check(load().merkle_sha3_256(_ptr(buf), n_leaves, leaf_bytes, ctypes.addressof(root), _stream(stream)),
+           "merkle_sha3_256")
+    return bytes(root)
+
+
+def merkle_node_count(n_leaves: int) -> int:
+    return int(load().merkle_node_count(n_leaves))
+
+
+def merkle_sha3_256_levels(buf, n_leaves: int, leaf_bytes: int, nodes, stream=None) -> None:
+    _check(load().merkle_sha3_256_levels(_ptr(buf), n_leaves, leaf_bytes, _ptr(nodes), _stream(stream)),
+           "merkle_sha3_256_levels")
+
+
+def keccak_last_error(stream=None) -> int:
+    return _check(load().keccak_last_error(_stream(stream)), "keccak_last_error")
+
+
+def keccak_release() -> None:
+    load().keccak_release()
+
+
+def round_constants() -> list[int]:
+    out = (ctypes.c_uint64 * 24)()
+    _check(load().sha3gb_round_constants(ctypes.addressof(out)), "sha3gb_round_constants")
+    return list(out)
+
+
+def rho_offsets() -> list[int]:
+    out = (ctypes.c_uint32 * 25)()
+    _check(load().sha3gb_rho_offsets(ctypes.addressof(out)), "sha3gb_rho_offsets")
+    return list(out)
+
+
+def int_issue_probe(op: int, iters: int = 4096, stream=None) -> float:
+    """Measured 32-bit integer thread-instructions per SM clock for one kind of
+    instruction: 0 LOP3, 1 SHF, 2 PRMT, 3 add."""
+    out = ctypes.c_double()
+    _check(load().sha3gb_int_issue_probe(op, iters, ctypes.addressof(out), _stream(stream)), "int_issue_probe")
+    return out.value
+
+
+def version() -> str:
+    return load().sha3gb_version().decode()

@@ -1,0 +1,230 @@
+// capi.cu -- the extern "C" entry points declared in include/sha3gb.h:
+// argument checks on the host, dispatch to the kernels, the pipelined
+// host-buffer path, status and constant queries.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+
+#include "keccak_core.cuh"
+#include "runtime.cuh"
+
+namespace kb {
+namespace {
+
+bool valid_out_len(int variant, uint32_t out_len) {
+    const int d = variant_digest(variant);
+    return d == 0 || out_len == uint32_t(d);
+}
+
+// Checks that (n-1)*stride + len and n*out_len fit in 64 bits.
+bool sizes_fit(uint64_t stride, uint64_t len, uint32_t out_len, uint64_t n) {
+    if (n == 0) return true;
+    if (stride != 0 && (n - 1) > (UINT64_MAX - len) / stride) return false;
+    if (out_len != 0 && n > UINT64_MAX / out_len) return false;
+    return true;
+}
+
+// ---- host-buffer pipeline ---------------------------------------------------
+constexpr int kStages = 3;
+
+struct Pipeline {
+    cudaStream_t streams[kStages] = {};
+    uint8_t *d_in[kStages] = {};
+    uint8_t *d_out[kStages] = {};
+    size_t in_bytes = 0, out_bytes = 0;
+    bool ready = false;
+};
+
+std::mutex g_pipe_mu;
+std::map<int, Pipeline> g_pipes;
+
+void free_pipeline(Pipeline &p) {
+    for (int s = 0; s < kStages; ++s) {
+        if (p.streams[s]) cudaStreamSynchronize(p.streams[s]);
+        if (p.d_in[s]) cudaFree(p.d_in[s]);
+        if (p.d_out[s]) cudaFree(p.d_out[s]);
+        if (p.streams[s]) cudaStreamDestroy(p.streams[s]);
+        p.streams[s] = nullptr;
+        p.d_in[s] = p.d_out[s] = nullptr;
+    }
+    p.in_bytes = p.out_bytes = 0;
+    p.ready = false;
+}
+
+int ensure_pipeline(Pipeline &p, size_t in_bytes, size_t out_bytes) {
+    if (!p.ready) {
+        for (int s = 0; s < kStages; ++s)
+            if (cudaStreamCreateWithFlags(&p.streams[s], cudaStreamNonBlocking) != cudaSuccess)
+                return KB_ERR_CUDA;
+        p.ready = true;
+    }
+    if (p.in_bytes < in_bytes || p.out_bytes < out_bytes) {
+        for (int s = 0; s < kStages; ++s) {
+            cudaStreamSynchronize(p.streams[s]);
+            if (p.d_in[s]) cudaFree(p.d_in[s]);
+            if (p.d_out[s]) cudaFree(p.d_out[s]);
+            p.d_in[s] = p.d_out[s] = nullptr;
+        }
+        p.in_bytes = std::max(p.in_bytes, in_bytes);
+        p.out_bytes = std::max(p.out_bytes, out_bytes);
+        for (int s = 0; s < kStages; ++s) {
+            if (cudaMalloc(&p.d_in[s], p.in_bytes ? p.in_bytes : 16) != cudaSuccess ||
+                cudaMalloc(&p.d_out[s], p.out_bytes ? p.out_bytes : 16) != cudaSuccess) {
+                cudaGetLastError();
+                free_pipeline(p);
+                return KB_ERR_NOMEM;
+            }
+        }
+    }
+    return KB_OK;
+}
+
+}  // namespace
+}  // namespace kb
+
+using namespace kb;
+
+extern "C" {
+
+int keccak_batch_uniform(const uint8_t *msgs, uint64_t stride, uint64_t len, int variant,
+                         uint32_t out_len, uint8_t *digests, uint64_t n, void *stream) {
+    if (variant < 0 || variant > 5 || !valid_out_len(variant, out_len)) return KB_ERR_INVALID;
+    if (n == 0) return KB_OK;
+    if ((len > 0 && !msgs) || (out_len > 0 && !digests) || !sizes_fit(stride, len, out_len, n))
+        return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    return launch_uniform(msgs, stride, len, variant, out_len, digests, n,
+                          static_cast<cudaStream_t>(stream), *dev);
+}
+
+int keccak_batch(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                 const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests,
+                 uint64_t n, void *stream) {
+    if (n == 0) return KB_OK;
+    if (!msgs || !offsets || !lens || !variant || !out_lens || !digests) return KB_ERR_INVALID;
+    if (n > (UINT64_MAX >> 4)) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    return launch_ragged(msgs, offsets, lens, variant, out_lens, digests, n,
+                         static_cast<cudaStream_t>(stream), *dev);
+}
+
+uint64_t merkle_node_count(uint64_t n_leaves) { return merkle_nodes(n_leaves); }
+
+int merkle_sha3_256_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes,
+                           uint8_t *nodes, void *stream) {
+    if (n_leaves == 0 || leaf_bytes == 0 || !buf || !nodes) return KB_ERR_INVALID;
+    if (n_leaves > UINT64_MAX / leaf_bytes || n_leaves > (UINT64_MAX >> 7)) return KB_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(nodes) & 31) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    return launch_merkle_levels(buf, n_leaves, leaf_bytes, nodes, static_cast<cudaStream_t>(stream), *dev);
+}
+
+int merkle_sha3_256(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *root,
+                    void *stream) {
+    if (n_leaves == 0 || leaf_bytes == 0 || !buf || !root) return KB_ERR_INVALID;
+    if (n_leaves > UINT64_MAX / leaf_bytes || n_leaves > (UINT64_MAX >> 7)) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t total = merkle_nodes(n_leaves);
+    uint8_t *nodes = static_cast<uint8_t *>(stream_scratch(s, size_t(32 * total), &err));
+    if (!nodes) return err;
+    if ((err = launch_merkle_levels(buf, n_leaves, leaf_bytes, nodes, s, *dev)) != KB_OK) return err;
+    if (cudaMemcpyAsync(root, nodes + 32 * (total - 1), 32, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return KB_ERR_CUDA;
+    return KB_OK;
+}
+
+int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t len, int variant,
+                              uint32_t out_len, uint8_t *h_digests, uint64_t n, void *stream) {
+    if (variant < 0 || variant > 5 || !valid_out_len(variant, out_len)) return KB_ERR_INVALID;
+    if (n == 0) return KB_OK;
+    if ((len > 0 && !h_msgs) || (out_len > 0 && !h_digests) || !sizes_fit(stride, len, out_len, n))
+        return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    // Chunks of about 32 MiB of input (at least one message each).
+    const uint64_t target = uint64_t(32) << 20;
+    uint64_t chunk = stride ? std::max<uint64_t>(1, target / stride) : n;
+    chunk = std::min(chunk, n);
+    const size_t in_bytes = size_t((chunk - 1) * stride + len);
+    const size_t out_bytes = size_t(chunk * out_len);
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    Pipeline &p = g_pipes[dev->device];
+    if ((err = ensure_pipeline(p, in_bytes, out_bytes)) != KB_OK) return err;
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    cudaEvent_t start;
+    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return KB_ERR_CUDA;
+    int rc = cuda_status(cudaEventRecord(start, user));
+    for (int s = 0; s < kStages && rc == KB_OK; ++s) rc = cuda_status(cudaStreamWaitEvent(p.streams[s], start, 0));
+    uint64_t idx = 0;
+    for (uint64_t first = 0; first < n && rc == KB_OK; first += chunk, ++idx) {
+        const int s = int(idx % kStages);
+        const uint64_t cnt = std::min(chunk, n - first);
+        const size_t span = size_t((cnt - 1) * stride + len);
+        if (span) rc = cuda_status(cudaMemcpyAsync(p.d_in[s], h_msgs + first * stride, span,
+                                                   cudaMemcpyHostToDevice, p.streams[s]));
+        if (rc == KB_OK)
+            rc = launch_uniform(p.d_in[s], stride, len, variant, out_len, p.d_out[s], cnt, p.streams[s], *dev);
+        if (rc == KB_OK && out_len)
+            rc = cuda_status(cudaMemcpyAsync(h_digests + first * out_len, p.d_out[s], size_t(cnt * out_len),
+                                             cudaMemcpyDeviceToHost, p.streams[s]));
+    }
+    for (int s = 0; s < kStages; ++s)
+        if (cudaStreamSynchronize(p.streams[s]) != cudaSuccess) rc = KB_ERR_CUDA;
+    cudaEventDestroy(start);
+    return rc;
+}
+
+int keccak_last_error(void *stream) {
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return KB_ERR_CUDA;
+    unsigned int word = 0;
+    if (cudaMemcpy(&word, dev->d_status, sizeof word, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(dev->d_status, 0, sizeof word) != cudaSuccess)
+        return KB_ERR_CUDA;
+    return int(word & 0x7fffffffu);
+}
+
+void keccak_release(void) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_pipe_mu);
+        auto it = g_pipes.find(dev);
+        if (it != g_pipes.end()) {
+            free_pipeline(it->second);
+            g_pipes.erase(it);
+        }
+    }
+    release_device();
+}
+
+int sha3gb_round_constants(uint64_t *rc24) {
+    if (!rc24) return KB_ERR_INVALID;
+    for (int i = 0; i < 24; ++i) rc24[i] = round_constant(i);
+    return KB_OK;
+}
+
+int sha3gb_rho_offsets(uint32_t *rho25) {
+    if (!rho25) return KB_ERR_INVALID;
+    for (int i = 0; i < 25; ++i) rho25[i] = uint32_t(rho_offset(i));
+    return KB_OK;
+}
+
+const char *sha3gb_version(void) { return "sha3gb 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,202 @@
+// merkle.cu -- tree mode (Section 4: messages "hashed in twos until the Hash
+// Root", named there as future work done with reductions).
+//
+// Node format: leaf = SHA3-256(0x00 || leaf bytes), inner node =
+// SHA3-256(0x01 || left || right); levels are reduced one at a time and an odd
+// last node is carried up unchanged.  All levels are written back to back
+// (leaf digests first, root last) so that callers can also take proofs.
+//
+// Kernels: one thread per leaf (the prefixed message is read through a
+// one-byte funnel shift of the leaf's aligned words), then one launch per
+// level with one thread per parent node (0x01 || left || right is exactly one
+// 65-byte block at rate 136).
+#include <cuda_runtime.h>
+
+#include "keccak_core.cuh"
+#include "runtime.cuh"
+#include "sponge.cuh"
+
+namespace kb {
+namespace {
+
+constexpr int kRate = Variant<1>::rate;   // SHA3-256
+constexpr int kDomain = Variant<1>::domain;
+
+// Lane word g of the virtual message 0x00 || leaf, built from leaf words g-1
+// and g: the byte that falls off the top of word g-1 becomes byte 0 of word g.
+// `carry` holds the high half of leaf word g-1 (prefix << 24 for g = 0).
+__device__ __forceinline__ void prefixed_word(uint32_t &carry, uint32_t lo, uint32_t hi, uint32_t &vlo,
+                                              uint32_t &vhi) {
+    vlo = __funnelshift_l(carry, lo, 8);
+    vhi = __funnelshift_l(lo, hi, 8);
+    carry = hi;
+}
+
+// Leaves at 8-byte aligned addresses with leaf_bytes % 8 == 0.
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_merkle_leaves_a8(const uint8_t *__restrict__ buf, uint64_t n_leaves, uint64_t leaf_bytes,
+                       uint8_t *__restrict__ out) {
+    const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t mwords = leaf_bytes / 8;          // leaf words
+    const uint64_t vlen = leaf_bytes + 1;            // prefixed message length
+    const uint64_t nfull = vlen / kRate;
+    const uint32_t rem = uint32_t(vlen - nfull * kRate);
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n_leaves; i += step) {
+        const uint8_t *p = buf + i * leaf_bytes;
+        uint32_t E[25], O[25];
+#pragma unroll
+        for (int k = 0; k < 25; ++k) E[k] = O[k] = 0;
+        uint32_t carry = 0x00u << 24;  // leaf prefix byte
+        for (uint64_t b = 0; b <= nfull; ++b) {
+            const uint64_t g0 = b * (kRate / 8);
+            if (b < nfull) {
+#pragma unroll
+                for (int k = 0; k < kRate / 8; ++k) {
+                    uint32_t lo, hi, vlo, vhi;
+                    ld_word_a8(p + 8 * (g0 + k), lo, hi);
+                    prefixed_word(carry, lo, hi, vlo, vhi);
+                    xor_lane(E[k], O[k], vlo, vhi);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kRate / 8; ++k) {
+                    uint32_t lo = 0, hi = 0, vlo, vhi;
+                    if (g0 + k < mwords) ld_word_a8(p + 8 * (g0 + k), lo, hi);
+                    prefixed_word(carry, lo, hi, vlo, vhi);
+                    if (uint32_t(k) == rem / 8) {
+                        const uint32_t sh = (rem % 8) * 8;
+                        if (sh < 32) vlo ^= uint32_t(kDomain) << sh;
+                        else vhi ^= uint32_t(kDomain) << (sh - 32);
+                    }
+                    if (k == kRate / 8 - 1) vhi ^= 0x80000000u;
+                    xor_lane(E[k], O[k], vlo, vhi);
+                }
+            }
+            keccak_f1600(E, O);
+        }
+        squeeze<kRate>(E, O, out + 32 * i, 32);
+    }
+}
+
+// Any alignment / leaf size: byte-exact reads through ld_word_any.
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_merkle_leaves_any(const uint8_t *__restrict__ buf, uint64_t n_leaves, uint64_t leaf_bytes,
+                        uint8_t *__restrict__ out) {
+    const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t vlen = leaf_bytes + 1;
+    const uint64_t nfull = vlen / kRate;
+    const uint32_t rem = uint32_t(vlen - nfull * kRate);
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n_leaves; i += step) {
+        const uint8_t *p = buf + i * leaf_bytes;
+        uint32_t E[25], O[25];
+#pragma unroll
+        for (int k = 0; k < 25; ++k) E[k] = O[k] = 0;
+        for (uint64_t b = 0; b <= nfull; ++b) {
+            const uint32_t valid = b < nfull ? uint32_t(kRate) : rem;  // virtual bytes in this block
+#pragma unroll
+            for (int k = 0; k < kRate / 8; ++k) {
+                // Virtual bytes [v0, v0 + 8) are leaf bytes [v0 - 1, v0 + 7).
+                const uint64_t v0 = b * kRate + 8 * k;
+                uint32_t lo = 0, hi = 0;
+                const uint32_t inblk = 8 * k;
+                if (inblk < valid) {
+                    const uint32_t nv = valid - inblk < 8 ? valid - inblk : 8;  // virtual bytes present
+                    if (v0 == 0) {
+                        if (nv > 1) ld_word_any(p, nv - 1, lo, hi);
+                        hi = __funnelshift_l(lo, hi, 8);
+                        lo = (lo << 8) | 0x00u;
+                    } else {
+                        ld_word_any(p + (v0 - 1), nv, lo, hi);
+                    }
+                }
+                if (b == nfull) {
+                    if (uint32_t(k) == rem / 8) {
+                        const uint32_t sh = (rem % 8) * 8;
+                        if (sh < 32) lo ^= uint32_t(kDomain) << sh;
+                        else hi ^= uint32_t(kDomain) << (sh - 32);
+                    }
+                    if (k == kRate / 8 - 1) hi ^= 0x80000000u;
+                }
+                xor_lane(E[k], O[k], lo, hi);
+            }
+            keccak_f1600(E, O);
+        }
+        squeeze<kRate>(E, O, out + 32 * i, 32);
+    }
+}
+
+// One level: parent j = SHA3-256(0x01 || in[2j] || in[2j+1]); for an odd
+// count the last child is copied to out[count/2].  `in` is 32-byte aligned.
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_merkle_level(const uint8_t *__restrict__ in, uint64_t count, uint8_t *__restrict__ out) {
+    const uint64_t pairs = count / 2;
+    const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < pairs + (count & 1); j += step) {
+        if (j == pairs) {
+            const uint4 *s = reinterpret_cast<const uint4 *>(in + 32 * (count - 1));
+            uint4 *d = reinterpret_cast<uint4 *>(out + 32 * j);
+            d[0] = s[0];
+            d[1] = s[1];
+            continue;
+        }
+        uint32_t E[25], O[25];
+#pragma unroll
+        for (int k = 0; k < 25; ++k) E[k] = O[k] = 0;
+        const uint4 *q = reinterpret_cast<const uint4 *>(in + 64 * j);
+        uint32_t carry = 0x01u << 24;  // node prefix byte
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const uint4 v = __ldg(q + t);
+            uint32_t vlo, vhi;
+            prefixed_word(carry, v.x, v.y, vlo, vhi);
+            to_interleaved(vlo, vhi, E[2 * t], O[2 * t]);
+            prefixed_word(carry, v.z, v.w, vlo, vhi);
+            to_interleaved(vlo, vhi, E[2 * t + 1], O[2 * t + 1]);
+        }
+        // Word 8: the last child byte, then the domain byte at message offset 65.
+        uint32_t vlo = (carry >> 24) | (uint32_t(kDomain) << 8), vhi = 0;
+        to_interleaved(vlo, vhi, E[8], O[8]);
+        E[kRate / 8 - 1] ^= even_half(uint64_t(0x80) << 56);
+        O[kRate / 8 - 1] ^= odd_half(uint64_t(0x80) << 56);
+        keccak_f1600(E, O);
+        squeeze<kRate>(E, O, out + 32 * j, 32);
+    }
+}
+
+}  // namespace
+
+uint64_t merkle_nodes(uint64_t n_leaves) {
+    if (n_leaves == 0) return 0;
+    uint64_t total = 0, n = n_leaves;
+    for (;;) {
+        total += n;
+        if (n == 1) break;
+        n = (n + 1) / 2;
+    }
+    return total;
+}
+
+int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes,
+                         cudaStream_t stream, const DeviceInfo &dev) {
+    const bool a8 = ((reinterpret_cast<uintptr_t>(buf) | leaf_bytes) & 7) == 0;
+    const void *fn = a8 ? reinterpret_cast<const void *>(&k_merkle_leaves_a8)
+                        : reinterpret_cast<const void *>(&k_merkle_leaves_any);
+    uint64_t grid = persistent_grid(fn, kThreads, 0, n_leaves, dev);
+    if (a8) k_merkle_leaves_a8<<<unsigned(grid), kThreads, 0, stream>>>(buf, n_leaves, leaf_bytes, nodes);
+    else k_merkle_leaves_any<<<unsigned(grid), kThreads, 0, stream>>>(buf, n_leaves, leaf_bytes, nodes);
+    if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
+    uint8_t *level = nodes;
+    uint64_t n = n_leaves;
+    while (n > 1) {
+        uint8_t *next = level + 32 * n;
+        const uint64_t parents = n / 2 + (n & 1);
+        grid = persistent_grid(reinterpret_cast<const void *>(&k_merkle_level), kThreads, 0, parents, dev);
+        k_merkle_level<<<unsigned(grid), kThreads, 0, stream>>>(level, n, next);
+        if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
+        level = next;
+        n = parents;
+    }
+    return KB_OK;
+}
+
+}  // namespace kb

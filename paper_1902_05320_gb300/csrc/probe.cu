@@ -1,0 +1,99 @@
+// probe.cu -- integer-issue microbenchmark behind the ALU roofline.
+//
+// Each thread runs eight interleaved dependency chains of one 32-bit integer
+// instruction (LOP3, SHF funnel rotate, PRMT or IADD3); every block of a
+// one-wave grid reads its SM clock before and after.  Lanes per clock per SM
+// = (instructions x 32 lanes issued on the SM) / elapsed SM cycles.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "runtime.cuh"
+
+namespace kb {
+namespace {
+
+constexpr int kProbeThreads = 256;
+
+template <int OP>
+__device__ __forceinline__ uint32_t probe_op(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    if constexpr (OP == 0) asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    else if constexpr (OP == 1) asm volatile("shf.l.wrap.b32 %0, %1, %2, 7;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 2) asm volatile("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(d) : "r"(a), "r"(b));
+    else asm volatile("add.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kProbeThreads)
+    k_int_probe(uint32_t iters, uint32_t seed, uint32_t *sink, long long *cycles) {
+    uint32_t a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = seed * (threadIdx.x + 1) + 0x9E3779B9u * (j + 1);
+    const uint32_t c = seed ^ blockIdx.x;
+    __syncthreads();
+    const long long t0 = clock64();
+#pragma unroll 4
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = probe_op<OP>(a[j], a[(j + 4) & 7], c + j);
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    uint32_t x = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x ^= a[j];
+    if (x == 0x12345678u) sink[blockIdx.x] = x;  // keeps the chains live
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+template <int OP>
+int run_probe(uint32_t iters, double *lanes_per_clk, cudaStream_t stream, const DeviceInfo &dev) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_int_probe<OP>, kProbeThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+        return KB_ERR_CUDA;
+    const int grid = per_sm * dev.sm_count;
+    uint32_t *sink = nullptr;
+    long long *cycles = nullptr;
+    if (cudaMalloc(&sink, sizeof(uint32_t) * grid) != cudaSuccess) return KB_ERR_NOMEM;
+    if (cudaMalloc(&cycles, sizeof(long long) * grid) != cudaSuccess) {
+        cudaFree(sink);
+        return KB_ERR_NOMEM;
+    }
+    k_int_probe<OP><<<grid, kProbeThreads, 0, stream>>>(iters, 12345u, sink, cycles);
+    std::vector<long long> h(grid);
+    int rc = cuda_status(cudaGetLastError());
+    if (rc == KB_OK) rc = cuda_status(cudaMemcpyAsync(h.data(), cycles, sizeof(long long) * grid,
+                                                      cudaMemcpyDeviceToHost, stream));
+    if (rc == KB_OK) rc = cuda_status(cudaStreamSynchronize(stream));
+    cudaFree(sink);
+    cudaFree(cycles);
+    if (rc != KB_OK) return rc;
+    double mean = 0;
+    for (long long v : h) mean += double(v);
+    mean /= grid;
+    const double instr_per_sm = double(iters) * 8.0 * kProbeThreads * per_sm;  // thread-instructions
+    *lanes_per_clk = instr_per_sm / mean;
+    return KB_OK;
+}
+
+}  // namespace
+}  // namespace kb
+
+using namespace kb;
+
+extern "C" int sha3gb_int_issue_probe(int op, uint32_t iters, double *lanes_per_clk_per_sm, void *stream) {
+    if (!lanes_per_clk_per_sm || op < 0 || op > 3 || iters == 0) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    switch (op) {
+        case 0: return run_probe<0>(iters, lanes_per_clk_per_sm, s, *dev);
+        case 1: return run_probe<1>(iters, lanes_per_clk_per_sm, s, *dev);
+        case 2: return run_probe<2>(iters, lanes_per_clk_per_sm, s, *dev);
+        default: return run_probe<3>(iters, lanes_per_clk_per_sm, s, *dev);
+    }
+}

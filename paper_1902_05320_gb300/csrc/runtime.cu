@@ -1,0 +1,119 @@
+// runtime.cu -- per-device state, per-stream scratch arenas and grid sizing.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <unordered_map>
+#include <utility>
+
+#include "runtime.cuh"
+
+namespace kb {
+namespace {
+
+struct Arena {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct DeviceSlot {
+    DeviceInfo info;
+    std::map<cudaStream_t, Arena> arenas;
+    std::unordered_map<const void *, int> occupancy;  // blocks/SM per (kernel, threads)
+};
+
+std::mutex g_mu;
+std::map<int, DeviceSlot> g_devices;
+
+DeviceSlot *slot_for_current(int *err) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        *err = KB_ERR_CUDA;
+        return nullptr;
+    }
+    auto it = g_devices.find(dev);
+    if (it != g_devices.end()) return &it->second;
+    DeviceSlot s;
+    s.info.device = dev;
+    if (cudaDeviceGetAttribute(&s.info.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaMalloc(&s.info.d_status, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(s.info.d_status, 0, sizeof(unsigned int)) != cudaSuccess) {
+        *err = KB_ERR_CUDA;
+        return nullptr;
+    }
+    return &g_devices.emplace(dev, std::move(s)).first->second;
+}
+
+}  // namespace
+
+DeviceInfo *device_info(int *err) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceSlot *s = slot_for_current(err);
+    return s ? &s->info : nullptr;
+}
+
+void *stream_scratch(cudaStream_t stream, size_t bytes, int *err) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceSlot *s = slot_for_current(err);
+    if (!s) return nullptr;
+    Arena &a = s->arenas[stream];
+    if (a.bytes >= bytes && a.ptr) return a.ptr;
+    if (a.ptr) {
+        // Work already enqueued on this stream may still use the old block.
+        if (cudaStreamSynchronize(stream) != cudaSuccess) {
+            *err = KB_ERR_CUDA;
+            return nullptr;
+        }
+        cudaFree(a.ptr);
+        a.ptr = nullptr;
+        a.bytes = 0;
+    }
+    size_t want = bytes < (size_t(1) << 20) ? (size_t(1) << 20) : bytes + bytes / 4;
+    if (cudaMalloc(&a.ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        a.ptr = nullptr;
+        *err = KB_ERR_NOMEM;
+        return nullptr;
+    }
+    a.bytes = want;
+    return a.ptr;
+}
+
+void release_device() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    auto it = g_devices.find(dev);
+    if (it == g_devices.end()) return;
+    cudaDeviceSynchronize();
+    for (auto &kv : it->second.arenas)
+        if (kv.second.ptr) cudaFree(kv.second.ptr);
+    if (it->second.info.d_status) cudaFree(it->second.info.d_status);
+    g_devices.erase(it);
+}
+
+uint64_t persistent_grid(const void *fn, int threads, size_t smem, uint64_t work_items,
+                         const DeviceInfo &dev) {
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto &slot = g_devices[dev.device];
+        auto it = slot.occupancy.find(fn);
+        if (it != slot.occupancy.end()) {
+            per_sm = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
+                per_sm < 1) {
+                cudaGetLastError();
+                per_sm = 1;
+            }
+            slot.occupancy[fn] = per_sm;
+        }
+    }
+    const uint64_t full = uint64_t(per_sm) * uint64_t(dev.sm_count);
+    const uint64_t need = (work_items + threads - 1) / threads;
+    uint64_t g = need < full ? need : full;
+    return g < 1 ? 1 : g;
+}
+
+}  // namespace kb

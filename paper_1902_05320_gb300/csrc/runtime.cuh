@@ -1,0 +1,56 @@
+// runtime.cuh -- host-side runtime shared by the library's translation units:
+// per-device state (SM count, the device status word), per-stream scratch
+// arenas, and the launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/sha3gb.h"
+
+namespace kb {
+
+// Threads per block of the thread-per-message kernels.
+constexpr int kThreads = 128;
+// Minimum resident blocks per SM asked of ptxas for the sponge kernels: caps
+// them at 128 registers per thread (16 warps per SM).
+constexpr int kMinBlocks = 4;
+
+struct DeviceInfo {
+    int device = -1;
+    int sm_count = 0;
+    unsigned int *d_status = nullptr;  // device status word (KB_DEV_* bits)
+};
+
+// State of the calling thread's current device, created on first use.
+// Returns nullptr (and sets *err) when the CUDA runtime fails.
+DeviceInfo *device_info(int *err);
+
+// A scratch arena cached per (device, stream): returns at least `bytes` of
+// device memory reserved for work enqueued on `stream`.  Growing the arena
+// synchronises the stream before the old block is freed.
+void *stream_scratch(cudaStream_t stream, size_t bytes, int *err);
+
+// Frees all cached state of the current device.
+void release_device();
+
+// Blocks of `threads` that keep every SM busy for kernel `fn` (occupancy x SMs),
+// capped by the number of blocks the work needs.
+uint64_t persistent_grid(const void *fn, int threads, size_t smem, uint64_t work_items,
+                         const DeviceInfo &dev);
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? KB_OK : KB_ERR_CUDA; }
+
+// Launchers (one per translation unit of kernels).
+int launch_uniform(const uint8_t *msgs, uint64_t stride, uint64_t len, int variant, uint32_t out_len,
+                   uint8_t *digests, uint64_t n, cudaStream_t stream, const DeviceInfo &dev);
+int launch_ragged(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
+                  const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
+                  const DeviceInfo &dev);
+uint64_t merkle_nodes(uint64_t n_leaves);
+int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes,
+                         cudaStream_t stream, const DeviceInfo &dev);
+
+}  // namespace kb

@@ -1,0 +1,60 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/sha3gb.h declares, carries the round constants and rho
+offsets the standard fixes, and rejects bad arguments before touching CUDA."""
+import ctypes
+
+import pytest
+
+from paper_1902_05320_gb300 import binding, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = binding.declared_functions()
+    assert {"keccak_batch", "keccak_batch_uniform", "merkle_sha3_256", "keccak_last_error"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_round_constants_match_oracle_lfsr(lib, oracle_mod):
+    # Definition 5 / Eq. 8: the kernels' immediates equal rc() regenerated by
+    # the oracle's FIPS 202 Algorithm 5 register.
+    assert binding.round_constants() == [oracle_mod.round_constant(6, ir) for ir in range(24)]
+
+
+def test_rho_offsets_match_oracle_walk(lib, oracle_mod):
+    want = [oracle_mod.rho_offset(64, i % 5, i // 5) for i in range(25)]
+    assert binding.rho_offsets() == want
+
+
+def test_version(lib):
+    assert "sm_103a" in binding.version()
+
+
+def test_argument_errors_are_returned_before_any_cuda_call(lib):
+    # Null pointers with n > 0, unknown variants and SHA3 output sizes other
+    # than the digest size are KB_ERR_INVALID; n = 0 is a no-op.
+    assert lib.keccak_batch_uniform(None, 64, 64, 1, 32, None, 0, None) == binding.KB_OK
+    assert lib.keccak_batch_uniform(None, 64, 64, 1, 32, None, 5, None) == binding.KB_ERR_INVALID
+    assert lib.keccak_batch_uniform(None, 64, 64, 6, 32, None, 0, None) == binding.KB_ERR_INVALID
+    assert lib.keccak_batch_uniform(None, 64, 64, 1, 31, None, 0, None) == binding.KB_ERR_INVALID
+    assert lib.keccak_batch_uniform(None, 64, 0, 4, 0, None, 0, None) == binding.KB_OK
+    assert lib.keccak_batch(None, None, None, None, None, None, 0, None) == binding.KB_OK
+    assert lib.keccak_batch(None, None, None, None, None, None, 3, None) == binding.KB_ERR_INVALID
+    assert lib.keccak_batch_uniform_host(None, 8, 8, 1, 32, None, 2, None) == binding.KB_ERR_INVALID
+    root = (ctypes.c_uint8 * 32)()
+    assert lib.merkle_sha3_256(None, 0, 8, ctypes.addressof(root), None) == binding.KB_ERR_INVALID
+    assert lib.merkle_sha3_256(1 << 20, 4, 0, ctypes.addressof(root), None) == binding.KB_ERR_INVALID
+    assert lib.merkle_sha3_256_levels(1 << 20, 0, 8, 1 << 20, None) == binding.KB_ERR_INVALID
+    # Overflowing sizes.
+    assert lib.keccak_batch_uniform(1 << 20, 1 << 40, 64, 1, 32, 1 << 20, 1 << 30, None) == binding.KB_ERR_INVALID
+
+
+def test_merkle_node_count(lib, oracle_mod):
+    for n in (0, 1, 2, 3, 5, 7, 8, 9, 1000, 524288):
+        assert binding.merkle_node_count(n) == oracle_mod.merkle_node_count(n)

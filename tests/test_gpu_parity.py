@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA library against the CPU oracle, bit for bit.
+
+Every digest is an exact function of its message (FIPS 202, which the paper
+restates in Section 3), so the tolerance is zero everywhere.  Inputs come from
+the seeded generators in paper_1902_05320_gb300.workloads; expected values only
+from the oracle (or, for the 4 GiB Merkle root, from hashlib).
+"""
+import hashlib
+import os
+
+import numpy as np
+import pytest
+
+from paper_1902_05320_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RATES = (144, 136, 104, 72, 168, 136)
+DIG = (28, 32, 48, 64, None, None)
+THREADS = len(os.sched_getaffinity(0))
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def dev(a: np.ndarray):
+    torch = _torch()
+    a = np.ascontiguousarray(a)
+    view = {np.dtype(np.uint64): np.int64, np.dtype(np.uint32): np.int32}.get(a.dtype)
+    t = torch.from_numpy(a.view(view) if view is not None else a)
+    return t.cuda()
+
+
+def host(t) -> np.ndarray:
+    _torch().cuda.synchronize()
+    return t.cpu().numpy().view(np.uint8).reshape(-1)
+
+
+def oracle_uniform(oracle_mod, msgs, stride, length, variant, out_len, n, idx=None):
+    idx = np.arange(n) if idx is None else np.asarray(idx)
+    offs = (idx.astype(np.uint64) * np.uint64(stride))
+    k = idx.size
+    return oracle_mod.hash_batch(msgs, offs, np.full(k, length, np.uint64), np.full(k, variant, np.uint8),
+                                 np.full(k, out_len, np.uint32), THREADS).reshape(k, out_len)
+
+
+def gpu_uniform(cuda_lib, msgs_np, stride, length, variant, out_len, n, base_shift=0):
+    torch = _torch()
+    buf = torch.zeros(msgs_np.size + base_shift + 16, dtype=torch.uint8, device="cuda")
+    if msgs_np.size:
+        buf[base_shift:base_shift + msgs_np.size] = dev(msgs_np)
+    out = torch.full((max(n * out_len, 1),), 0xEE, dtype=torch.uint8, device="cuda")
+    cuda_lib.keccak_batch_uniform(buf.data_ptr() + base_shift, stride, length, variant, out_len, out, n)
+    return host(out)[: n * out_len].reshape(n, out_len)
+
+
+# -- the 4096 x 64 B SHA3-256 batch, every digest ----------------------------------
+def test_sha3_256_4096_messages_of_64_bytes(cuda_lib, oracle_mod):
+    n, L = 4096, 64
+    msgs = W.uniform_messages(n, L, seed=0)
+    got = gpu_uniform(cuda_lib, msgs, L, L, 1, 32, n)
+    want = oracle_uniform(oracle_mod, msgs, L, L, 1, 32, n)
+    assert np.array_equal(got, want)
+
+
+# -- fixed-stride batches: every variant, padding boundary and alignment ------------
+@pytest.mark.parametrize("variant", range(6))
+def test_uniform_lengths_and_alignments(cuda_lib, oracle_mod, variant):
+    r = RATES[variant]
+    rng = np.random.default_rng(100 + variant)
+    n = 200  # spans two 128-thread blocks with a ragged tail
+    for L in (0, 1, 7, 8, 63, 64, 65, r - 2, r - 1, r, r + 1, 2 * r + 3, 700):
+        out_len = DIG[variant] or int(rng.choice([0, 1, 32, r - 1, r, r + 1, 2 * r + 5]))
+        for stride, shift in ((-(-max(L, 1) // 16) * 16, 0), (L + 3, 1), (L, 2)):
+            stride = max(stride, 1) if L == 0 else stride
+            msgs = W.random_bytes((n - 1) * stride + L, seed=int(rng.integers(1 << 30)))
+            got = gpu_uniform(cuda_lib, msgs, stride, L, variant, out_len, n, base_shift=shift)
+            want = oracle_uniform(oracle_mod, msgs, stride, L, variant, out_len, n)
+            assert np.array_equal(got, want), (variant, L, stride, shift, out_len)
+
+
+def test_uniform_zero_stride_and_single_message(cuda_lib, oracle_mod):
+    msgs = W.random_bytes(300, seed=5)
+    got = gpu_uniform(cuda_lib, msgs, 0, 300, 3, 64, 37)
+    want = oracle_mod.hash(3, msgs.tobytes())
+    assert all(row.tobytes() == want for row in got)
+    got1 = gpu_uniform(cuda_lib, msgs, 300, 300, 5, 1000, 1)
+    assert got1[0].tobytes() == oracle_mod.hash(5, msgs.tobytes(), 1000)
+
+
+# -- ragged, mixed-variant batches ----------------------------------------------------
+def _run_ragged(cuda_lib, b: W.RaggedBatch, sentinel=0xEE):
+    torch = _torch()
+    out = torch.full((max(b.total_out(), 1),), sentinel, dtype=torch.uint8, device="cuda")
+    cuda_lib.keccak_batch(dev(b.msgs), dev(b.offsets), dev(b.lens), dev(b.variants), dev(b.out_lens), out, b.n)
+    return host(out)[: b.total_out()]
+
+
+def _oracle_ragged(oracle_mod, b: W.RaggedBatch):
+    return oracle_mod.hash_batch(b.msgs, b.offsets, b.lens, b.variants, b.out_lens, THREADS)
+
+
+@pytest.mark.parametrize("seed,n,max_len,gap", [(11, 3000, 1500, 7), (12, 300, 65536, 3), (13, 1, 50, 0),
+                                                (14, 129, 300, 0)])
+def test_ragged_batch_matches_oracle(cuda_lib, oracle_mod, seed, n, max_len, gap):
+    b = W.ragged_batch(n, seed=seed, max_len=max_len, gap=gap)
+    assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
+    assert cuda_lib.keccak_last_error() == 0
+
+
+def test_ragged_every_padding_case(cuda_lib, oracle_mod):
+    # For each variant: len mod r in {0, 1, r-2, r-1} plus the empty message.
+    lens, variants = [], []
+    for v in range(6):
+        r = RATES[v]
+        for L in (0, 1, r - 2, r - 1, r, r + 1, 2 * r - 1, 2 * r):
+            lens.append(L)
+            variants.append(v)
+    rng = np.random.default_rng(3)
+    order = rng.permutation(len(lens))
+    b = W.ragged_batch(len(lens), seed=21, lens=np.array(lens)[order], gap=5)
+    b.variants = np.array(variants, dtype=np.uint8)[order]
+    b.out_lens = np.array([DIG[v] or int(rng.integers(0, 600)) for v in b.variants], dtype=np.uint32)
+    assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
+
+
+def test_ragged_same_digest_alone_and_in_the_mix(cuda_lib):
+    torch = _torch()
+    b = W.ragged_batch(500, seed=31, max_len=4000, gap=3)
+    mixed = _run_ragged(cuda_lib, b)
+    oo = b.out_offsets()
+    d_msgs = dev(b.msgs)
+    for i in np.random.default_rng(0).choice(b.n, size=25, replace=False):
+        out = torch.zeros(max(int(b.out_lens[i]), 1), dtype=torch.uint8, device="cuda")
+        cuda_lib.keccak_batch(d_msgs, dev(b.offsets[i:i + 1]), dev(b.lens[i:i + 1]), dev(b.variants[i:i + 1]),
+                              dev(b.out_lens[i:i + 1]), out, 1)
+        alone = host(out)[: int(b.out_lens[i])]
+        assert np.array_equal(alone, mixed[int(oo[i]):int(oo[i]) + int(b.out_lens[i])]), i
+
+
+def test_ragged_bad_messages_are_flagged_and_skipped(cuda_lib, oracle_mod):
+    b = W.ragged_batch(64, seed=41, max_len=500, variants=(1, 3))
+    b.variants[5] = 9          # no such variant
+    b.out_lens[7] = 31 if b.variants[7] == 1 else 63  # wrong SHA3 digest size
+    assert cuda_lib.keccak_last_error() == 0
+    got = _run_ragged(cuda_lib, b, sentinel=0xEE)
+    status = cuda_lib.keccak_last_error()
+    assert status & 0x1 and status & 0x2
+    assert cuda_lib.keccak_last_error() == 0  # cleared by the read
+    oo = b.out_offsets()
+    for i in range(b.n):
+        seg = got[int(oo[i]):int(oo[i]) + int(b.out_lens[i])]
+        if i in (5, 7):
+            assert (seg == 0xEE).all()
+        else:
+            want = oracle_mod.hash(int(b.variants[i]), b.msgs[int(b.offsets[i]):int(b.offsets[i] + b.lens[i])],
+                                   int(b.out_lens[i]))
+            assert seg.tobytes() == want
+
+
+# -- Merkle trees ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n_leaves,leaf_bytes", [(1, 8), (2, 64), (3, 135), (5, 136), (7, 1001), (8, 8192),
+                                                 (9, 7), (33, 200), (100, 64), (1000, 32), (64, 8192)])
+def test_merkle_levels_and_root(cuda_lib, oracle_mod, n_leaves, leaf_bytes):
+    torch = _torch()
+    buf = W.merkle_buffer(n_leaves, leaf_bytes, seed=n_leaves * 1000 + leaf_bytes)
+    want = oracle_mod.merkle_levels(buf, n_leaves, leaf_bytes)
+    d_buf = dev(buf)
+    total = cuda_lib.merkle_node_count(n_leaves)
+    nodes = torch.zeros(32 * total, dtype=torch.uint8, device="cuda")
+    cuda_lib.merkle_sha3_256_levels(d_buf, n_leaves, leaf_bytes, nodes)
+    assert np.array_equal(host(nodes).reshape(total, 32), want)
+    assert cuda_lib.merkle_sha3_256(d_buf, n_leaves, leaf_bytes) == want[-1].tobytes()
+
+
+def test_merkle_unaligned_buffer(cuda_lib, oracle_mod):
+    torch = _torch()
+    n, lb = 17, 96
+    buf = W.merkle_buffer(n, lb, seed=77)
+    raw = torch.zeros(buf.size + 8, dtype=torch.uint8, device="cuda")
+    raw[3:3 + buf.size] = dev(buf)
+    assert cuda_lib.merkle_sha3_256(raw.data_ptr() + 3, n, lb) == oracle_mod.merkle_root(buf, n, lb)
+
+
+# -- host-buffer pipeline ---------------------------------------------------------------------
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_pipeline_matches_oracle(cuda_lib, oracle_mod, pinned):
+    torch = _torch()
+    n, L = 700_000, 64  # 44.8 MB of input: more than one 32 MiB chunk
+    msgs = W.uniform_messages(n, L, seed=51)
+    if pinned:
+        h_in = torch.from_numpy(msgs).pin_memory()
+        h_out = torch.zeros(n * 32, dtype=torch.uint8).pin_memory()
+    else:
+        h_in, h_out = msgs, np.zeros(n * 32, dtype=np.uint8)
+    cuda_lib.keccak_batch_uniform_host(h_in, L, L, 1, 32, h_out, n)
+    got = (h_out.numpy() if pinned else h_out).reshape(n, 32)
+    chunk = (32 << 20) // L
+    idx = np.unique(np.concatenate([np.arange(5), np.arange(chunk - 3, chunk + 3), np.arange(n - 5, n),
+                                    np.random.default_rng(1).choice(n, 2000, replace=False)]))
+    want = oracle_uniform(oracle_mod, msgs, L, L, 1, 32, n, idx)
+    assert np.array_equal(got[idx], want)
+
+
+# -- full benchmark sizes, sampled ---------------------------------------------------------------
+def test_full_size_fixed_batches_sampled(cuda_lib, oracle_mod):
+    torch = _torch()
+    n, L = 1 << 24, 64
+    msgs = W.uniform_messages(n, L, seed=1)
+    d_msgs = dev(msgs)
+    rng = np.random.default_rng(2)
+    idx = np.unique(np.concatenate([np.arange(64), np.arange(n - 64, n), rng.choice(n, 4096, replace=False)]))
+    for variant, dl in ((1, 32), (3, 64)):
+        out = torch.zeros(n * dl, dtype=torch.uint8, device="cuda")
+        cuda_lib.keccak_batch_uniform(d_msgs, L, L, variant, dl, out, n)
+        got = host(out).reshape(n, dl)
+        assert np.array_equal(got[idx], oracle_uniform(oracle_mod, msgs, L, L, variant, dl, n, idx)), variant
+        del out
+    del d_msgs
+    n2, L2 = 1 << 22, 1024
+    msgs2 = W.uniform_messages(n2, L2, seed=2)
+    d2 = dev(msgs2)
+    out2 = torch.zeros(n2 * 32, dtype=torch.uint8, device="cuda")
+    cuda_lib.keccak_batch_uniform(d2, L2, L2, 1, 32, out2, n2)
+    got2 = host(out2).reshape(n2, 32)
+    idx2 = np.unique(np.concatenate([np.arange(16), np.arange(n2 - 16, n2), rng.choice(n2, 1024, replace=False)]))
+    assert np.array_equal(got2[idx2], oracle_uniform(oracle_mod, msgs2, L2, L2, 1, 32, n2, idx2))
+
+
+def test_full_size_ragged_batch_sampled(cuda_lib, oracle_mod):
+    b = W.ragged_batch(1 << 20, seed=3, max_len=65536)
+    got = _run_ragged(cuda_lib, b)
+    oo = b.out_offsets()
+    rng = np.random.default_rng(4)
+    longest = np.argsort(b.lens)[-8:]
+    idx = np.unique(np.concatenate([np.arange(32), np.arange(b.n - 32, b.n), longest,
+                                    rng.choice(b.n, 400, replace=False)]))
+    sub = W.RaggedBatch(b.msgs, b.offsets[idx], b.lens[idx], b.variants[idx], b.out_lens[idx])
+    want = _oracle_ragged(oracle_mod, sub)
+    pos = 0
+    for i in idx:
+        ln = int(b.out_lens[i])
+        assert np.array_equal(got[int(oo[i]):int(oo[i]) + ln], want[pos:pos + ln]), i
+        pos += ln
+    assert cuda_lib.keccak_last_error() == 0
+
+
+def test_full_size_merkle_root(cuda_lib, oracle_mod):
+    torch = _torch()
+    n, lb = 524288, 8192
+    buf = W.merkle_buffer(n, lb, seed=4)
+    d_buf = dev(buf)
+    total = cuda_lib.merkle_node_count(n)
+    nodes = torch.zeros(32 * total, dtype=torch.uint8, device="cuda")
+    cuda_lib.merkle_sha3_256_levels(d_buf, n, lb, nodes)
+    got = host(nodes).reshape(total, 32)
+    root = cuda_lib.merkle_sha3_256(d_buf, n, lb)
+    assert root == got[-1].tobytes()
+    # Sampled leaves against the oracle.
+    for i in np.random.default_rng(5).choice(n, 16, replace=False):
+        assert got[i].tobytes() == oracle_mod.hash(1, b"\x00" + buf[i * lb:(i + 1) * lb].tobytes())
+    # Every level from its children, and the leaves, with hashlib (independent of both).
+    leaves = [hashlib.sha3_256(b"\x00" + buf[i * lb:(i + 1) * lb].tobytes()).digest() for i in range(n)]
+    assert all(got[i].tobytes() == leaves[i] for i in range(n))
+    level, pos = leaves, n
+    while len(level) > 1:
+        nxt = [hashlib.sha3_256(b"\x01" + level[2 * j] + level[2 * j + 1]).digest() for j in range(len(level) // 2)]
+        if len(level) % 2:
+            nxt.append(level[-1])
+        assert all(got[pos + j].tobytes() == nxt[j] for j in range(len(nxt)))
+        pos += len(nxt)
+        level = nxt
+    assert root == level[0]
