@@ -50,7 +50,7 @@ ROUND_OPS_NO_IOTA = 20 + 5 + 50 + 47 + 50
 # issue roofline (see the design doc for the derivation and the probe that
 # confirms the lane count).
 SM_COUNT_GB300 = 152
-INT_LANES_PER_SM_CLK = 128
+INT_LANES_PER_SM_CLK = 64
 SM_MAX_MHZ = 2070.0
 
 
@@ -209,6 +209,9 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--messages", type=int, default=N_MSGS,
+                    help="messages per step (default 2^24; smaller only for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -230,13 +233,14 @@ def main() -> None:
     build.build()
     binding.load()
 
-    msgs_np = workloads.uniform_messages(N_MSGS, MSG_BYTES, seed=1 + rank)
+    n_msgs = args.messages
+    msgs_np = workloads.uniform_messages(n_msgs, MSG_BYTES, seed=1 + rank)
     msgs = torch.from_numpy(msgs_np).cuda()
-    digests = torch.empty(N_MSGS * DIGEST, dtype=torch.uint8, device="cuda")
+    digests = torch.empty(n_msgs * DIGEST, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
-        binding.keccak_batch_uniform(msgs, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, digests, N_MSGS, stream)
+        binding.keccak_batch_uniform(msgs, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, digests, n_msgs, stream)
 
     for _ in range(args.warmup):
         step()
@@ -273,25 +277,28 @@ def main() -> None:
         ms = float(t.item())
     clocks = sampler.summary()
 
-    value = world * N_MSGS / (ms / 1e3) / 1e6
+    value = world * n_msgs / (ms / 1e3) / 1e6
     ops_perm = ops_per_permutation()
-    achieved = N_MSGS * ops_perm / (ms / 1e3) / 1e12
+    achieved = n_msgs * ops_perm / (ms / 1e3) / 1e12
     peak = SM_COUNT_GB300 * INT_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     traffic = measured_traffic()
 
     # End to end through the host-buffer entry point (copies in the timed region).
-    h_in = torch.from_numpy(msgs_np).pin_memory()
-    h_out = torch.empty(N_MSGS * DIGEST, dtype=torch.uint8).pin_memory()
-    e2e_steps = max(3, min(args.steps, 10))
-    binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, N_MSGS, stream)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for _ in range(e2e_steps):
-        binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, N_MSGS, stream)
-    e2e_s = (time.perf_counter() - t) / e2e_steps
-    if not torch.equal(h_out[: 1 << 20], digests[: 1 << 20].cpu()):
-        raise SystemExit("host-buffer path disagrees with the device path")
-    e2e_value = world * N_MSGS / e2e_s / 1e6
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(msgs_np).pin_memory()
+        h_out = torch.empty(n_msgs * DIGEST, dtype=torch.uint8).pin_memory()
+        e2e_steps = max(3, min(args.steps, 10))
+        binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, n_msgs, stream)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(e2e_steps):
+            binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, n_msgs, stream)
+        e2e_s = (time.perf_counter() - t) / e2e_steps
+        if not torch.equal(h_out[: 1 << 20], digests[: 1 << 20].cpu()):
+            raise SystemExit("host-buffer path disagrees with the device path")
+        e2e = {"value": world * n_msgs / e2e_s / 1e6, "unit": "Mhash/s", "h2d_bytes_per_step": n_msgs * MSG_BYTES,
+               "d2h_bytes_per_step": n_msgs * DIGEST, "entry_point": "keccak_batch_uniform_host (pinned)"}
 
     extra = {} if args.no_extra else extra_measurements(binding, workloads, torch, stream, msgs, rank)
     del msgs, digests
@@ -300,25 +307,25 @@ def main() -> None:
         "metric": METRIC, "value": value, "unit": "Mhash/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "messages_per_gpu": N_MSGS, "msg_bytes": MSG_BYTES,
+        "config": {"workload": WORKLOAD if n_msgs == N_MSGS else f"sha3_256_{n_msgs}_msgs_x_64B",
+                   "messages_per_gpu": n_msgs, "msg_bytes": MSG_BYTES,
                    "variant": "SHA3-256", "entry_point": "keccak_batch_uniform",
                    "l2": "inputs (1 GiB per step) larger than L2; no flush", "parallelism": f"replicas{world}"},
-        "gb_per_s": world * N_MSGS * MSG_BYTES / (ms / 1e3) / 1e9,
+        "gb_per_s": world * n_msgs * MSG_BYTES / (ms / 1e3) / 1e9,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "ops_per_hash": ops_perm,
                      "peak_basis": f"{SM_COUNT_GB300} SMs x {INT_LANES_PER_SM_CLK} int32 lanes/clk x "
                                    f"{SM_MAX_MHZ:.0f} MHz max SM clock",
                      "kernel": "k_sha3_uniform<SHA3-256, 64 B>"},
-        "e2e": {"value": e2e_value, "unit": "Mhash/s", "h2d_bytes_per_step": N_MSGS * MSG_BYTES,
-                "d2h_bytes_per_step": N_MSGS * DIGEST, "entry_point": "keccak_batch_uniform_host (pinned)"},
+        "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
     if extra:
         line["extra"] = extra
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(msgs_np)
+        line["cpu_baseline"] = cpu_baseline(msgs_np[: min(n_msgs, N_MSGS) * MSG_BYTES])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -341,9 +348,19 @@ def extra_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    d64 = torch.empty(N_MSGS * 64, dtype=torch.uint8, device="cuda")
-    ms = timed(lambda: binding.keccak_batch_uniform(msgs, 64, 64, 3, 64, d64, N_MSGS, stream))
-    out["sha3_512_2p24_x_64B_mhash_s"] = N_MSGS / ms / 1e3
+    n = msgs.numel() // MSG_BYTES
+    # The bit-interleaved state layout, the measured control for the default.
+    d32 = torch.empty(n * 32, dtype=torch.uint8, device="cuda")
+    binding.keccak_tune_set(binding.KB_TUNE_REPRESENTATION, binding.KB_REP_INTERLEAVED)
+    try:
+        ms = timed(lambda: binding.keccak_batch_uniform(msgs, 64, 64, 1, 32, d32, n, stream))
+    finally:
+        binding.keccak_tune_set(binding.KB_TUNE_REPRESENTATION, binding.KB_REP_PLAIN)
+    out["sha3_256_2p24_x_64B_interleaved_control_mhash_s"] = n / ms / 1e3
+    del d32
+    d64 = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
+    ms = timed(lambda: binding.keccak_batch_uniform(msgs, 64, 64, 3, 64, d64, n, stream))
+    out["sha3_512_2p24_x_64B_mhash_s"] = n / ms / 1e3
     del d64
     n2, l2 = 1 << 22, 1024
     m2 = torch.from_numpy(workloads.uniform_messages(n2, l2, seed=2 + rank)).cuda()

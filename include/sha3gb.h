@@ -152,6 +152,21 @@ int keccak_last_error(void *stream);
  * of this library is in flight. */
 void keccak_release(void);
 
+/* Process-wide tuning knobs.  keccak_tune_set returns KB_OK or KB_ERR_INVALID
+ * (unknown key or value); keccak_tune_get returns the value or -1 for an
+ * unknown key.  Changing a knob affects calls issued afterwards.
+ *   KB_TUNE_REPRESENTATION: register layout of the Keccak state in the
+ *     fixed-stride SHA3-256 kernels -- KB_REP_PLAIN (default: 32-bit low/high
+ *     halves of each lane) or KB_REP_INTERLEAVED (even/odd bit halves, the
+ *     layout whose rotations need fewer funnel shifts but whose every message
+ *     word must be bit-interleaved; kept as a measured control).  Other
+ *     variants always use the plain layout. */
+#define KB_TUNE_REPRESENTATION 0
+#define KB_REP_PLAIN 0
+#define KB_REP_INTERLEAVED 1
+int keccak_tune_set(int key, int64_t value);
+int64_t keccak_tune_get(int key);
+
 /* The 24 round constants (Definition 5, Eq. 8-9) and 25 rho offsets (lane
  * index x+5y) compiled into the kernels, written to HOST arrays, so that
  * tests can compare them with an independent generation. */

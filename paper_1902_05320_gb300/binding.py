@@ -60,6 +60,8 @@ _SIGS = {
     "sha3gb_round_constants": (ctypes.c_int, [ctypes.c_void_p]),
     "sha3gb_rho_offsets": (ctypes.c_int, [ctypes.c_void_p]),
     "sha3gb_version": (ctypes.c_char_p, []),
+    "keccak_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64]),
+    "keccak_tune_get": (ctypes.c_int64, [ctypes.c_int]),
     "sha3gb_int_issue_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
@@ -149,6 +151,18 @@ def keccak_last_error(stream=None) -> int:
 
 def keccak_release() -> None:
     load().keccak_release()
+
+
+KB_TUNE_REPRESENTATION = 0
+KB_REP_PLAIN, KB_REP_INTERLEAVED = 0, 1
+
+
+def keccak_tune_set(key: int, value: int) -> None:
+    _check(load().keccak_tune_set(key, value), "keccak_tune_set")
+
+
+def keccak_tune_get(key: int) -> int:
+    return int(load().keccak_tune_get(key))
 
 
 def round_constants() -> list[int]:

@@ -225,6 +225,10 @@ int sha3gb_rho_offsets(uint32_t *rho25) {
     return KB_OK;
 }
 
+int keccak_tune_set(int key, int64_t value) { return tuning_set(key, value); }
+
+int64_t keccak_tune_get(int key) { return tuning_get(key); }
+
 const char *sha3gb_version(void) { return "sha3gb 0.1.0 (sm_103a)"; }
 
 }  // extern "C"

@@ -1,30 +1,38 @@
 // keccak_core.cuh -- device primitives of the batch SHA-3 library (sm_103a).
 //
-// State representation.  The 1600-bit state is 25 lanes of 64 bits, lane
-// index i = x + 5y (Eq. 1, lane bit z = state bit 64(5y+x)+z).  Each lane is
-// held in registers as two 32-bit halves in bit-interleaved form: E holds the
-// lane's even bits (bit 2k of the lane is bit k of E), O its odd bits.  A
-// 64-bit rotation by n then becomes two 32-bit rotations (one SHF each, none
-// when the amount is 0): by n/2 on both halves for even n; for odd n the
-// halves swap, E' = rotl(O, (n+1)/2) and O' = rotl(E, (n-1)/2).
+// The 1600-bit state is 25 lanes of 64 bits, lane index i = x + 5y (Eq. 1:
+// lane bit z is state bit 64(5y+x)+z).  It lives in registers as 50 32-bit
+// words, in one of two representations chosen at compile time:
 //
-// Round function (Eq. 10), per 32-bit half:
-//   theta (Eq. 2-4): column parities C (two 3-input XOR LOP3s per half), the
-//     rotated parity rot(C[x+1], 1) (one SHF per column: the odd-half part of
-//     a rotation by 1 is a plain register rename), then each half-lane gets
-//     A ^ C[x-1] ^ rot(C[x+1],1) in one 3-input LOP3.
-//   rho (Eq. 5, as FIPS 202 Algorithm 2) + pi (Eq. 6): constant SHF amounts
-//     and a compile-time renaming of registers; pi costs no instruction.
-//   chi (Eq. 7): a ^ (~b & c), one LOP3 per half-lane.
-//   iota (Eq. 8-9, the paper's "zeta"): XOR of compile-time immediates into
-//     lane (0,0); a half whose constant is 0 costs nothing.
-// That is at most 20 + 5 + 50 + 47 + 50 + 2 = 174 integer instructions per
-// round.
+//  * PlainRep (the default): lane i is (L[i], H[i]) = its low and high 32-bit
+//    halves, i.e. the little-endian message words themselves.  A 64-bit
+//    rotation by n is two SHF funnel shifts (none for n = 0, a register swap
+//    for n = 32).
+//  * InterleavedRep: lane i is (E[i], O[i]) = its even and odd bits.  A 64-bit
+//    rotation becomes two 32-bit rotations, which saves 6 SHF per round
+//    (theta's rotation by 1 and rho's offset-1 lane need one SHF instead of
+//    two), but every absorbed or squeezed 64-bit word costs 26 instructions of
+//    bit interleaving.  On sm_103a's half-rate integer pipe the conversion
+//    outweighs the saving for every message size, so this form is kept as the
+//    measured control.
 //
-// Round constants and rho offsets are computed at compile time by constexpr
-// restatements of FIPS 202 Algorithm 5 (the LFSR rc) and of the rho walk, so
-// the kernels carry them as instruction immediates (the paper kept them in
-// constant memory, Section 4.2).
+// Round function (Eq. 10), per 32-bit word, written as LOP3 and SHF:
+//   theta (Eq. 2-4): column parities C (two 3-input XORs per word), the
+//     rotated parity rot(C[x+1], 1), then A ^ C[x-1] ^ rot(C[x+1], 1) in one
+//     3-input LOP3 per word;
+//   rho (Eq. 5, as FIPS 202 Algorithm 2) + pi (Eq. 6): constant funnel shifts
+//     and a compile-time renaming of registers (pi costs nothing);
+//   chi (Eq. 7): a ^ (~b & c), one LOP3 per word;
+//   iota (Eq. 8-9, the paper's "zeta"): XOR of the round constant into lane 0.
+// Plain form: 20 + 10 + 50 + 48 + 50 + 2 = 180 instructions per round.
+//
+// Round structure: the first rounds run in a loop of four rounds per
+// iteration that reads the round constants from a __constant__ table (the
+// placement Section 4.2 uses) -- a fully unrolled 24-round body is larger
+// than the instruction cache serves well; the last four rounds are unrolled
+// with the constants as immediates, so when only a few output lanes are used
+// the compiler drops the rest of the final round.  Round 0 can be peeled the
+// same way when most of the input state is known to be zero.
 #pragma once
 
 #include <cstdint>
@@ -69,7 +77,7 @@ __host__ __device__ constexpr int rho_offset(int lane) {
     return -1;
 }
 
-// Even / odd bits of a 64-bit constant, for interleaving immediates.
+// Even / odd bits of a 64-bit value (interleaved representation).
 __host__ __device__ constexpr uint32_t even_half(uint64_t v) {
     uint32_t r = 0;
     for (int k = 0; k < 32; ++k) r |= uint32_t((v >> (2 * k)) & 1) << k;
@@ -80,6 +88,20 @@ __host__ __device__ constexpr uint32_t odd_half(uint64_t v) {
     for (int k = 0; k < 32; ++k) r |= uint32_t((v >> (2 * k + 1)) & 1) << k;
     return r;
 }
+
+// The round constants as (low, high) 32-bit words, for the looped rounds.
+struct RcTable {
+    uint32_t w[48];
+};
+__host__ __device__ constexpr RcTable make_rc_table() {
+    RcTable t{};
+    for (int i = 0; i < 24; ++i) {
+        t.w[2 * i] = uint32_t(round_constant(i));
+        t.w[2 * i + 1] = uint32_t(round_constant(i) >> 32);
+    }
+    return t;
+}
+static __constant__ RcTable c_rc = make_rc_table();
 
 // ---- instruction wrappers -----------------------------------------------------
 
@@ -96,135 +118,164 @@ __device__ __forceinline__ uint32_t chi3(uint32_t a, uint32_t b, uint32_t c) {
     return d;
 }
 
+// Upper 32 bits of (hi:lo) << N, 0 < N < 32 (one SHF).
+template <int N>
+__device__ __forceinline__ uint32_t funnel_l(uint32_t lo, uint32_t hi) {
+    uint32_t d;
+    asm("shf.l.wrap.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(lo), "r"(hi), "n"(N));
+    return d;
+}
+
 template <int N>
 __device__ __forceinline__ uint32_t rotl32(uint32_t x) {
-    if constexpr ((N & 31) == 0) {
-        return x;
+    if constexpr ((N & 31) == 0) return x;
+    else return funnel_l<(N & 31)>(x, x);
+}
+
+// ---- plain representation: 64-bit rotation of (lo, hi) ------------------------
+
+template <int N>
+__device__ __forceinline__ void rotl64(uint32_t lo, uint32_t hi, uint32_t &nl, uint32_t &nh) {
+    if constexpr (N == 0) {
+        nl = lo;
+        nh = hi;
+    } else if constexpr (N == 32) {
+        nl = hi;
+        nh = lo;
+    } else if constexpr (N < 32) {
+        nh = funnel_l<N>(lo, hi);
+        nl = funnel_l<N>(hi, lo);
     } else {
-        uint32_t d;
-        asm("shf.l.wrap.b32 %0, %1, %1, %2;" : "=r"(d) : "r"(x), "n"(N & 31));
-        return d;
+        nh = funnel_l<N - 32>(hi, lo);
+        nl = funnel_l<N - 32>(lo, hi);
     }
 }
 
-__device__ __forceinline__ uint32_t rotl32_1(uint32_t x) { return rotl32<1>(x); }
-
-// ---- bit interleaving ---------------------------------------------------------
-
-// Gathers the even bits of x into its low 16 bits and the odd bits into its
-// high 16 bits (an inverse perfect shuffle made of four delta swaps).
-__host__ __device__ __forceinline__ uint32_t unshuffle32(uint32_t x) {
-    uint32_t t;
-    t = (x ^ (x >> 1)) & 0x22222222u; x ^= t ^ (t << 1);
-    t = (x ^ (x >> 2)) & 0x0C0C0C0Cu; x ^= t ^ (t << 2);
-    t = (x ^ (x >> 4)) & 0x00F000F0u; x ^= t ^ (t << 4);
-    t = (x ^ (x >> 8)) & 0x0000FF00u; x ^= t ^ (t << 8);
-    return x;
-}
-
-// Inverse of unshuffle32.
-__host__ __device__ __forceinline__ uint32_t shuffle32(uint32_t x) {
-    uint32_t t;
-    t = (x ^ (x >> 8)) & 0x0000FF00u; x ^= t ^ (t << 8);
-    t = (x ^ (x >> 4)) & 0x00F000F0u; x ^= t ^ (t << 4);
-    t = (x ^ (x >> 2)) & 0x0C0C0C0Cu; x ^= t ^ (t << 2);
-    t = (x ^ (x >> 1)) & 0x22222222u; x ^= t ^ (t << 1);
-    return x;
-}
-
-// 64-bit little-endian lane (lo = bytes 0..3, hi = bytes 4..7) -> (E, O).
-__device__ __forceinline__ void to_interleaved(uint32_t lo, uint32_t hi, uint32_t &e, uint32_t &o) {
-    lo = unshuffle32(lo);
-    hi = unshuffle32(hi);
-    e = __byte_perm(lo, hi, 0x5410);
-    o = __byte_perm(lo, hi, 0x7632);
-}
-
-// (E, O) -> 64-bit little-endian lane halves.
-__device__ __forceinline__ void from_interleaved(uint32_t e, uint32_t o, uint32_t &lo, uint32_t &hi) {
-    lo = shuffle32(__byte_perm(e, o, 0x5410));
-    hi = shuffle32(__byte_perm(e, o, 0x7632));
-}
-
-// ---- the permutation ------------------------------------------------------------
-
-// theta's column terms for one source lane, then rho: writes the rotated
-// half-lanes that pi places at (x, y).  SX is the source column.
+// theta's column terms for the source lane of (X, Y), then rho; pi is the
+// choice of source: Eq. 6, A'[x,y] = A[(x+3y) mod 5, x].
 template <int X, int Y>
-__device__ __forceinline__ void theta_rho_pi(const uint32_t (&E)[25], const uint32_t (&O)[25],
-                                             const uint32_t (&CE)[5], const uint32_t (&CO)[5],
-                                             const uint32_t (&RE)[5], uint32_t &be, uint32_t &bo) {
-    constexpr int SX = (X + 3 * Y) % 5;  // Eq. 6: A'[x,y] = A[(x+3y) mod 5, x]
+__device__ __forceinline__ void plain_theta_rho_pi(const uint32_t (&L)[25], const uint32_t (&H)[25],
+                                                   const uint32_t (&CL)[5], const uint32_t (&CH)[5],
+                                                   const uint32_t (&RL)[5], const uint32_t (&RH)[5],
+                                                   uint32_t &bl, uint32_t &bh) {
+    constexpr int SX = (X + 3 * Y) % 5;
     constexpr int SRC = SX + 5 * X;
-    constexpr int N = rho_offset(SRC);
-    // Eq. 4 with D[x] = C[x-1] ^ rot(C[x+1], 1); in interleaved form the even
-    // half of rot(C,1) is rotl(C_odd, 1) and its odd half is C_even.
-    const uint32_t te = xor3(E[SRC], CE[(SX + 4) % 5], RE[(SX + 1) % 5]);
-    const uint32_t to = xor3(O[SRC], CO[(SX + 4) % 5], CE[(SX + 1) % 5]);
-    if constexpr ((N & 1) == 0) {
-        be = rotl32<N / 2>(te);
-        bo = rotl32<N / 2>(to);
-    } else {
-        be = rotl32<(N + 1) / 2>(to);
-        bo = rotl32<(N - 1) / 2>(te);
-    }
+    // Eq. 4 with D[x] = C[x-1] ^ rot(C[x+1], 1) (Eq. 3).
+    const uint32_t tl = xor3(L[SRC], CL[(SX + 4) % 5], RL[(SX + 1) % 5]);
+    const uint32_t th = xor3(H[SRC], CH[(SX + 4) % 5], RH[(SX + 1) % 5]);
+    rotl64<rho_offset(SRC)>(tl, th, bl, bh);
 }
 
 template <int Y>
-__device__ __forceinline__ void round_row(const uint32_t (&E)[25], const uint32_t (&O)[25],
-                                          const uint32_t (&CE)[5], const uint32_t (&CO)[5],
-                                          const uint32_t (&RE)[5], uint32_t (&NE)[25],
-                                          uint32_t (&NO)[25]) {
-    uint32_t BE[5], BO[5];
-    theta_rho_pi<0, Y>(E, O, CE, CO, RE, BE[0], BO[0]);
-    theta_rho_pi<1, Y>(E, O, CE, CO, RE, BE[1], BO[1]);
-    theta_rho_pi<2, Y>(E, O, CE, CO, RE, BE[2], BO[2]);
-    theta_rho_pi<3, Y>(E, O, CE, CO, RE, BE[3], BO[3]);
-    theta_rho_pi<4, Y>(E, O, CE, CO, RE, BE[4], BO[4]);
+__device__ __forceinline__ void plain_row(const uint32_t (&L)[25], const uint32_t (&H)[25], const uint32_t (&CL)[5],
+                                          const uint32_t (&CH)[5], const uint32_t (&RL)[5], const uint32_t (&RH)[5],
+                                          uint32_t (&NL)[25], uint32_t (&NH)[25]) {
+    uint32_t BL[5], BH[5];
+    plain_theta_rho_pi<0, Y>(L, H, CL, CH, RL, RH, BL[0], BH[0]);
+    plain_theta_rho_pi<1, Y>(L, H, CL, CH, RL, RH, BL[1], BH[1]);
+    plain_theta_rho_pi<2, Y>(L, H, CL, CH, RL, RH, BL[2], BH[2]);
+    plain_theta_rho_pi<3, Y>(L, H, CL, CH, RL, RH, BL[3], BH[3]);
+    plain_theta_rho_pi<4, Y>(L, H, CL, CH, RL, RH, BL[4], BH[4]);
 #pragma unroll
-    for (int x = 0; x < 5; ++x) {
-        NE[x + 5 * Y] = chi3(BE[x], BE[(x + 1) % 5], BE[(x + 2) % 5]);
-        NO[x + 5 * Y] = chi3(BO[x], BO[(x + 1) % 5], BO[(x + 2) % 5]);
+    for (int x = 0; x < 5; ++x) {  // Eq. 7
+        NL[x + 5 * Y] = chi3(BL[x], BL[(x + 1) % 5], BL[(x + 2) % 5]);
+        NH[x + 5 * Y] = chi3(BH[x], BH[(x + 1) % 5], BH[(x + 2) % 5]);
     }
 }
 
-template <int IR>
-__device__ __forceinline__ void keccak_round(uint32_t (&E)[25], uint32_t (&O)[25]) {
-    uint32_t CE[5], CO[5], RE[5];
+// One round without iota; the caller XORs the round constant into lane 0.
+__device__ __forceinline__ void plain_round_body(uint32_t (&L)[25], uint32_t (&H)[25], uint32_t (&NL)[25],
+                                                 uint32_t (&NH)[25]) {
+    uint32_t CL[5], CH[5], RL[5], RH[5];
 #pragma unroll
-    for (int x = 0; x < 5; ++x) {
-        CE[x] = xor3(xor3(E[x], E[x + 5], E[x + 10]), E[x + 15], E[x + 20]);
-        CO[x] = xor3(xor3(O[x], O[x + 5], O[x + 10]), O[x + 15], O[x + 20]);
+    for (int x = 0; x < 5; ++x) {  // Eq. 2
+        CL[x] = xor3(xor3(L[x], L[x + 5], L[x + 10]), L[x + 15], L[x + 20]);
+        CH[x] = xor3(xor3(H[x], H[x + 5], H[x + 10]), H[x + 15], H[x + 20]);
     }
 #pragma unroll
-    for (int x = 0; x < 5; ++x) RE[x] = rotl32_1(CO[x]);
-    uint32_t NE[25], NO[25];
-    round_row<0>(E, O, CE, CO, RE, NE, NO);
-    round_row<1>(E, O, CE, CO, RE, NE, NO);
-    round_row<2>(E, O, CE, CO, RE, NE, NO);
-    round_row<3>(E, O, CE, CO, RE, NE, NO);
-    round_row<4>(E, O, CE, CO, RE, NE, NO);
-    constexpr uint64_t RC = round_constant(IR);
-    constexpr uint32_t RCE = even_half(RC), RCO = odd_half(RC);
-    if constexpr (RCE != 0) NE[0] ^= RCE;
-    if constexpr (RCO != 0) NO[0] ^= RCO;
+    for (int x = 0; x < 5; ++x) rotl64<1>(CL[x], CH[x], RL[x], RH[x]);
+    plain_row<0>(L, H, CL, CH, RL, RH, NL, NH);
+    plain_row<1>(L, H, CL, CH, RL, RH, NL, NH);
+    plain_row<2>(L, H, CL, CH, RL, RH, NL, NH);
+    plain_row<3>(L, H, CL, CH, RL, RH, NL, NH);
+    plain_row<4>(L, H, CL, CH, RL, RH, NL, NH);
+}
+
+// Round i_r with its constant read from the __constant__ table.
+__device__ __forceinline__ void plain_round_rt(uint32_t (&L)[25], uint32_t (&H)[25], int ir) {
+    uint32_t NL[25], NH[25];
+    plain_round_body(L, H, NL, NH);
+    NL[0] ^= c_rc.w[2 * ir];  // Eq. 9
+    NH[0] ^= c_rc.w[2 * ir + 1];
 #pragma unroll
     for (int i = 0; i < 25; ++i) {
-        E[i] = NE[i];
-        O[i] = NO[i];
+        L[i] = NL[i];
+        H[i] = NH[i];
     }
 }
 
-template <int... IR>
-__device__ __forceinline__ void keccak_rounds(uint32_t (&E)[25], uint32_t (&O)[25],
-                                              std::integer_sequence<int, IR...>) {
-    (keccak_round<IR>(E, O), ...);
+// Round IR with its constant as an immediate.
+template <int IR>
+__device__ __forceinline__ void plain_round_ct(uint32_t (&L)[25], uint32_t (&H)[25]) {
+    constexpr uint64_t RC = round_constant(IR);
+    uint32_t NL[25], NH[25];
+    plain_round_body(L, H, NL, NH);
+    if constexpr (uint32_t(RC) != 0) NL[0] ^= uint32_t(RC);
+    if constexpr (uint32_t(RC >> 32) != 0) NH[0] ^= uint32_t(RC >> 32);
+#pragma unroll
+    for (int i = 0; i < 25; ++i) {
+        L[i] = NL[i];
+        H[i] = NH[i];
+    }
 }
 
-// Keccak-f[1600] = Keccak-p[1600, 24], rounds i_r = 0..23, fully unrolled.
-__device__ __forceinline__ void keccak_f1600(uint32_t (&E)[25], uint32_t (&O)[25]) {
-    keccak_rounds(E, O, std::make_integer_sequence<int, 24>{});
+template <int FIRST, int... K>
+__device__ __forceinline__ void plain_rounds_ct(uint32_t (&L)[25], uint32_t (&H)[25],
+                                                std::integer_sequence<int, K...>) {
+    (plain_round_ct<FIRST + K>(L, H), ...);
 }
+
+// Keccak-f[1600] = Keccak-p[1600, 24] (Eq. 10, i_r = 0..23).  PEEL0 runs
+// round 0 with an immediate constant so that known-zero input lanes fold.
+template <bool PEEL0>
+__device__ __forceinline__ void keccak_f1600_plain(uint32_t (&L)[25], uint32_t (&H)[25]) {
+    constexpr int kLoopUnroll = 4;
+    constexpr int kFirst = PEEL0 ? 1 : 0;
+    constexpr int kTail = PEEL0 ? 21 : 20;  // rounds [kTail, 24) unrolled
+    if constexpr (PEEL0) plain_round_ct<0>(L, H);
+#pragma unroll 1
+    for (int r = kFirst; r < kTail; r += kLoopUnroll) {
+#pragma unroll
+        for (int j = 0; j < kLoopUnroll; ++j) plain_round_rt(L, H, r + j);
+    }
+    plain_rounds_ct<kTail>(L, H, std::make_integer_sequence<int, 24 - kTail>{});
+}
+
+// ---- representations ------------------------------------------------------------
+
+struct PlainRep {
+    static constexpr const char *name = "plain";
+    // 64-bit little-endian word (lo, hi) <-> the lane's two state words.
+    __device__ __forceinline__ static void xor_word(uint32_t &a, uint32_t &b, uint32_t lo, uint32_t hi) {
+        a ^= lo;
+        b ^= hi;
+    }
+    __device__ __forceinline__ static void set_word(uint32_t &a, uint32_t &b, uint32_t lo, uint32_t hi) {
+        a = lo;
+        b = hi;
+    }
+    __device__ __forceinline__ static void get_word(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi) {
+        lo = a;
+        hi = b;
+    }
+    // A compile-time 64-bit lane value in this representation.
+    __host__ __device__ static constexpr uint32_t word_a(uint64_t v) { return uint32_t(v); }
+    __host__ __device__ static constexpr uint32_t word_b(uint64_t v) { return uint32_t(v >> 32); }
+    template <bool PEEL0>
+    __device__ __forceinline__ static void permute(uint32_t (&A)[25], uint32_t (&B)[25]) {
+        keccak_f1600_plain<PEEL0>(A, B);
+    }
+};
 
 // ---- variants -----------------------------------------------------------------
 

@@ -43,9 +43,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     const uint32_t rem = uint32_t(vlen - nfull * kRate);
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n_leaves; i += step) {
         const uint8_t *p = buf + i * leaf_bytes;
-        uint32_t E[25], O[25];
+        uint32_t A[25], B[25];
 #pragma unroll
-        for (int k = 0; k < 25; ++k) E[k] = O[k] = 0;
+        for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
         uint32_t carry = 0x00u << 24;  // leaf prefix byte
         for (uint64_t b = 0; b <= nfull; ++b) {
             const uint64_t g0 = b * (kRate / 8);
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
                     uint32_t lo, hi, vlo, vhi;
                     ld_word_a8(p + 8 * (g0 + k), lo, hi);
                     prefixed_word(carry, lo, hi, vlo, vhi);
-                    xor_lane(E[k], O[k], vlo, vhi);
+                    PlainRep::xor_word(A[k], B[k], vlo, vhi);
                 }
             } else {
 #pragma unroll
@@ -69,12 +69,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
                         else vhi ^= uint32_t(kDomain) << (sh - 32);
                     }
                     if (k == kRate / 8 - 1) vhi ^= 0x80000000u;
-                    xor_lane(E[k], O[k], vlo, vhi);
+                    PlainRep::xor_word(A[k], B[k], vlo, vhi);
                 }
             }
-            keccak_f1600(E, O);
+            PlainRep::permute<false>(A, B);
         }
-        squeeze<kRate>(E, O, out + 32 * i, 32);
+        squeeze<kRate, PlainRep>(A, B, out + 32 * i, 32);
     }
 }
 
@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     const uint32_t rem = uint32_t(vlen - nfull * kRate);
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n_leaves; i += step) {
         const uint8_t *p = buf + i * leaf_bytes;
-        uint32_t E[25], O[25];
+        uint32_t A[25], B[25];
 #pragma unroll
-        for (int k = 0; k < 25; ++k) E[k] = O[k] = 0;
+        for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
         for (uint64_t b = 0; b <= nfull; ++b) {
             const uint32_t valid = b < nfull ? uint32_t(kRate) : rem;  // virtual bytes in this block
 #pragma unroll
@@ -117,11 +117,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
                     }
                     if (k == kRate / 8 - 1) hi ^= 0x80000000u;
                 }
-                xor_lane(E[k], O[k], lo, hi);
+                PlainRep::xor_word(A[k], B[k], lo, hi);
             }
-            keccak_f1600(E, O);
+            PlainRep::permute<false>(A, B);
         }
-        squeeze<kRate>(E, O, out + 32 * i, 32);
+        squeeze<kRate, PlainRep>(A, B, out + 32 * i, 32);
     }
 }
 
@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
             d[1] = s[1];
             continue;
         }
-        uint32_t E[25], O[25];
+        uint32_t A[25], B[25];
 #pragma unroll
-        for (int k = 0; k < 25; ++k) E[k] = O[k] = 0;
+        for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
         const uint4 *q = reinterpret_cast<const uint4 *>(in + 64 * j);
         uint32_t carry = 0x01u << 24;  // node prefix byte
 #pragma unroll
@@ -149,17 +149,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
             const uint4 v = __ldg(q + t);
             uint32_t vlo, vhi;
             prefixed_word(carry, v.x, v.y, vlo, vhi);
-            to_interleaved(vlo, vhi, E[2 * t], O[2 * t]);
+            PlainRep::set_word(A[2 * t], B[2 * t], vlo, vhi);
             prefixed_word(carry, v.z, v.w, vlo, vhi);
-            to_interleaved(vlo, vhi, E[2 * t + 1], O[2 * t + 1]);
+            PlainRep::set_word(A[2 * t + 1], B[2 * t + 1], vlo, vhi);
         }
         // Word 8: the last child byte, then the domain byte at message offset 65.
         uint32_t vlo = (carry >> 24) | (uint32_t(kDomain) << 8), vhi = 0;
-        to_interleaved(vlo, vhi, E[8], O[8]);
-        E[kRate / 8 - 1] ^= even_half(uint64_t(0x80) << 56);
-        O[kRate / 8 - 1] ^= odd_half(uint64_t(0x80) << 56);
-        keccak_f1600(E, O);
-        squeeze<kRate>(E, O, out + 32 * j, 32);
+        PlainRep::set_word(A[8], B[8], vlo, vhi);
+        B[kRate / 8 - 1] ^= 0x80000000u;
+        PlainRep::permute<true>(A, B);
+        squeeze<kRate, PlainRep>(A, B, out + 32 * j, 32);
     }
 }
 

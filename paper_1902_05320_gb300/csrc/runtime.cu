@@ -1,6 +1,7 @@
 // runtime.cu -- per-device state, per-stream scratch arenas and grid sizing.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <unordered_map>
@@ -90,6 +91,25 @@ void release_device() {
         if (kv.second.ptr) cudaFree(kv.second.ptr);
     if (it->second.info.d_status) cudaFree(it->second.info.d_status);
     g_devices.erase(it);
+}
+
+namespace {
+constexpr int kTuneKeys = 1;
+std::atomic<int64_t> g_tuning[kTuneKeys] = {{KB_REP_PLAIN}};
+}  // namespace
+
+int64_t tuning_get(int key) { return (key >= 0 && key < kTuneKeys) ? g_tuning[key].load() : -1; }
+
+int tuning_set(int key, int64_t value) {
+    switch (key) {
+        case KB_TUNE_REPRESENTATION:
+            if (value != KB_REP_PLAIN && value != KB_REP_INTERLEAVED) return KB_ERR_INVALID;
+            break;
+        default:
+            return KB_ERR_INVALID;
+    }
+    g_tuning[key].store(value);
+    return KB_OK;
 }
 
 uint64_t persistent_grid(const void *fn, int threads, size_t smem, uint64_t work_items,

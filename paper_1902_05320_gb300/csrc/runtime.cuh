@@ -43,6 +43,10 @@ uint64_t persistent_grid(const void *fn, int threads, size_t smem, uint64_t work
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? KB_OK : KB_ERR_CUDA; }
 
+// Process-wide tuning knobs (kb_tune_key values of sha3gb.h).
+int64_t tuning_get(int key);
+int tuning_set(int key, int64_t value);
+
 // Launchers (one per translation unit of kernels).
 int launch_uniform(const uint8_t *msgs, uint64_t stride, uint64_t len, int variant, uint32_t out_len,
                    uint8_t *digests, uint64_t n, cudaStream_t stream, const DeviceInfo &dev);

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
             atomicOr(status, KB_DEV_BAD_OUTLEN);
             continue;
         }
-        sponge_rt<false>(msgs + offsets[i], lens[i], v, digests + out_off[i], dlen);
+        sponge_rt<false, PlainRep>(msgs + offsets[i], lens[i], v, digests + out_off[i], dlen);
     }
 }
 

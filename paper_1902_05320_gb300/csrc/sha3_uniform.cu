@@ -3,12 +3,16 @@
 // message the same length and variant (Section 4.3).
 //
 // Specialisations: for each variant, a compile-time 64-byte message read with
-// four 16-byte loads (one rate block: the padding folds into constants), a
-// runtime length with 8-byte aligned loads, and a runtime length at any
-// alignment.  A grid of (occupancy x SMs) blocks strides over the messages.
+// four 16-byte loads (one rate block: the padding folds into constants and
+// round 0 runs on mostly-zero lanes), a runtime length with 8-byte aligned
+// loads, and a runtime length at any alignment.  The state representation is
+// a template parameter: plain 32-bit halves by default, bit-interleaved
+// halves as the measured control for SHA3-256.  A grid of (occupancy x SMs)
+// blocks strides over the messages.
 #include <cuda_runtime.h>
 
 #include "keccak_core.cuh"
+#include "keccak_interleaved.cuh"
 #include "runtime.cuh"
 #include "sponge.cuh"
 
@@ -17,7 +21,7 @@ namespace {
 
 // LEN >= 0: compile-time message length; -1: runtime.  A8: base and stride are
 // multiples of 8 (16 when LEN == 64).
-template <int V, int LEN, bool A8>
+template <int V, int LEN, bool A8, class Rep>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     k_sha3_uniform(const uint8_t *__restrict__ msgs, uint64_t stride, uint64_t len_rt,
                    uint8_t *__restrict__ out, uint32_t out_len, uint64_t n) {
@@ -30,41 +34,41 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
         uint8_t *dst = out + m * dlen;
         if constexpr (LEN == 64) {
             static_assert(64 < P::rate, "a 64-byte message is one block for every variant");
-            uint32_t E[25], O[25];
+            uint32_t A[25], B[25];
 #pragma unroll
-            for (int i = 0; i < 25; ++i) E[i] = O[i] = 0;
+            for (int i = 0; i < 25; ++i) A[i] = B[i] = 0;
             const uint4 *q = reinterpret_cast<const uint4 *>(p);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const uint4 v = __ldg(q + j);
-                to_interleaved(v.x, v.y, E[2 * j], O[2 * j]);
-                to_interleaved(v.z, v.w, E[2 * j + 1], O[2 * j + 1]);
+                Rep::set_word(A[2 * j], B[2 * j], v.x, v.y);
+                Rep::set_word(A[2 * j + 1], B[2 * j + 1], v.z, v.w);
             }
             // Domain byte at offset 64 (lane 8, byte 0); 0x80 at byte rate-1.
-            E[8] ^= even_half(uint64_t(P::domain));
-            O[8] ^= odd_half(uint64_t(P::domain));
+            A[8] ^= Rep::word_a(uint64_t(P::domain));
+            B[8] ^= Rep::word_b(uint64_t(P::domain));
             constexpr uint64_t kEnd = uint64_t(0x80) << 56;
-            E[P::rate / 8 - 1] ^= even_half(kEnd);
-            O[P::rate / 8 - 1] ^= odd_half(kEnd);
+            A[P::rate / 8 - 1] ^= Rep::word_a(kEnd);
+            B[P::rate / 8 - 1] ^= Rep::word_b(kEnd);
             const uint32_t nsq = dlen > uint32_t(P::rate) ? (dlen - 1) / P::rate : 0;
             for (uint32_t i = 0; i <= nsq; ++i) {
-                if (i > 0) squeeze<P::rate>(E, O, dst + uint64_t(i - 1) * P::rate, P::rate);
-                keccak_f1600(E, O);
+                if (i > 0) squeeze<P::rate, Rep>(A, B, dst + uint64_t(i - 1) * P::rate, P::rate);
+                Rep::template permute<true>(A, B);
             }
-            squeeze<P::rate>(E, O, dst + uint64_t(nsq) * P::rate, dlen - nsq * P::rate);
+            squeeze<P::rate, Rep>(A, B, dst + uint64_t(nsq) * P::rate, dlen - nsq * P::rate);
         } else {
-            sponge<P::rate, P::domain, A8>(p, len, dst, dlen);
+            sponge<P::rate, P::domain, A8, Rep>(p, len, dst, dlen);
         }
     }
 }
 
-template <int V, int LEN, bool A8>
+template <int V, int LEN, bool A8, class Rep>
 int launch_one(const uint8_t *msgs, uint64_t stride, uint64_t len, uint32_t out_len, uint8_t *digests,
                uint64_t n, cudaStream_t stream, const DeviceInfo &dev) {
-    const void *fn = reinterpret_cast<const void *>(&k_sha3_uniform<V, LEN, A8>);
+    const void *fn = reinterpret_cast<const void *>(&k_sha3_uniform<V, LEN, A8, Rep>);
     const uint64_t grid = persistent_grid(fn, kThreads, 0, n, dev);
-    k_sha3_uniform<V, LEN, A8><<<unsigned(grid), kThreads, 0, stream>>>(msgs, stride, len, digests,
-                                                                         out_len, n);
+    k_sha3_uniform<V, LEN, A8, Rep><<<unsigned(grid), kThreads, 0, stream>>>(msgs, stride, len, digests,
+                                                                              out_len, n);
     return cuda_status(cudaGetLastError());
 }
 
@@ -74,9 +78,17 @@ int launch_variant(const uint8_t *msgs, uint64_t stride, uint64_t len, uint32_t 
     const uintptr_t base = reinterpret_cast<uintptr_t>(msgs);
     const bool a16 = ((base | stride) & 15) == 0;
     const bool a8 = ((base | stride) & 7) == 0;
-    if (len == 64 && a16) return launch_one<V, 64, true>(msgs, stride, len, out_len, digests, n, stream, dev);
-    if (a8) return launch_one<V, -1, true>(msgs, stride, len, out_len, digests, n, stream, dev);
-    return launch_one<V, -1, false>(msgs, stride, len, out_len, digests, n, stream, dev);
+    if constexpr (V == 1) {
+        // The bit-interleaved control, selected through the tuning interface.
+        if (tuning_get(KB_TUNE_REPRESENTATION) == KB_REP_INTERLEAVED) {
+            if (len == 64 && a16)
+                return launch_one<V, 64, true, InterleavedRep>(msgs, stride, len, out_len, digests, n, stream, dev);
+            if (a8) return launch_one<V, -1, true, InterleavedRep>(msgs, stride, len, out_len, digests, n, stream, dev);
+        }
+    }
+    if (len == 64 && a16) return launch_one<V, 64, true, PlainRep>(msgs, stride, len, out_len, digests, n, stream, dev);
+    if (a8) return launch_one<V, -1, true, PlainRep>(msgs, stride, len, out_len, digests, n, stream, dev);
+    return launch_one<V, -1, false, PlainRep>(msgs, stride, len, out_len, digests, n, stream, dev);
 }
 
 }  // namespace

@@ -1,5 +1,6 @@
 // sponge.cuh -- absorb / pad / squeeze of the Keccak[c] sponge (Section 3.2,
-// Eq. 11-18) on the bit-interleaved register state of keccak_core.cuh.
+// Eq. 11-18) on a register state of keccak_core.cuh, generic over the state
+// representation (PlainRep or InterleavedRep).
 //
 // Byte form of the padding: for a message of len bytes and rate r bytes, the
 // last block holds the len mod r remaining bytes, then the domain byte (the
@@ -28,8 +29,7 @@ __device__ __forceinline__ void ld_word_a8(const uint8_t *p, uint32_t &lo, uint3
 // Bytes [p, p + nvalid) as a little-endian 64-bit word, 1 <= nvalid <= 8, any
 // alignment; bytes past nvalid read as zero.  Loads only the aligned 32-bit
 // words that hold a valid byte.
-__device__ __forceinline__ void ld_word_any(const uint8_t *p, uint32_t nvalid, uint32_t &lo,
-                                            uint32_t &hi) {
+__device__ __forceinline__ void ld_word_any(const uint8_t *p, uint32_t nvalid, uint32_t &lo, uint32_t &hi) {
     const uintptr_t start = reinterpret_cast<uintptr_t>(p);
     const uint32_t *a = reinterpret_cast<const uint32_t *>(start & ~uintptr_t(3));
     const uint32_t sh = uint32_t(start & 3) * 8;
@@ -47,23 +47,15 @@ __device__ __forceinline__ void ld_word_any(const uint8_t *p, uint32_t nvalid, u
     }
 }
 
-// XOR one 64-bit message word into lane k.
-__device__ __forceinline__ void xor_lane(uint32_t &e, uint32_t &o, uint32_t lo, uint32_t hi) {
-    uint32_t we, wo;
-    to_interleaved(lo, hi, we, wo);
-    e ^= we;
-    o ^= wo;
-}
-
 // Absorbs one full block of RATE bytes at p (p 8-byte aligned when A8).
-template <int RATE, bool A8>
-__device__ __forceinline__ void absorb_full(uint32_t (&E)[25], uint32_t (&O)[25], const uint8_t *p) {
+template <int RATE, bool A8, class Rep>
+__device__ __forceinline__ void absorb_full(uint32_t (&A)[25], uint32_t (&B)[25], const uint8_t *p) {
     if constexpr (A8) {
 #pragma unroll
         for (int k = 0; k < RATE / 8; ++k) {
             uint32_t lo, hi;
             ld_word_a8(p + 8 * k, lo, hi);
-            xor_lane(E[k], O[k], lo, hi);
+            Rep::xor_word(A[k], B[k], lo, hi);
         }
     } else {
         // RATE/4 aligned words cover the block; one more when p is unaligned.
@@ -78,15 +70,15 @@ __device__ __forceinline__ void absorb_full(uint32_t (&E)[25], uint32_t (&O)[25]
             const uint32_t lo = __funnelshift_r(prev, w1, sh);
             const uint32_t hi = __funnelshift_r(w1, w2, sh);
             prev = w2;
-            xor_lane(E[k], O[k], lo, hi);
+            Rep::xor_word(A[k], B[k], lo, hi);
         }
     }
 }
 
 // Absorbs the final, padded block: rem (0 <= rem < RATE) message bytes at p,
 // then the domain byte at rem and 0x80 at RATE-1.
-template <int RATE, int DOMAIN, bool A8>
-__device__ __forceinline__ void absorb_last(uint32_t (&E)[25], uint32_t (&O)[25], const uint8_t *p,
+template <int RATE, int DOMAIN, bool A8, class Rep>
+__device__ __forceinline__ void absorb_last(uint32_t (&A)[25], uint32_t (&B)[25], const uint8_t *p,
                                             uint32_t rem) {
 #pragma unroll
     for (int k = 0; k < RATE / 8; ++k) {
@@ -103,14 +95,14 @@ __device__ __forceinline__ void absorb_last(uint32_t (&E)[25], uint32_t (&O)[25]
             else hi ^= uint32_t(DOMAIN) << (sh - 32);
         }
         if (k == RATE / 8 - 1) hi ^= 0x80000000u;
-        xor_lane(E[k], O[k], lo, hi);
+        Rep::xor_word(A[k], B[k], lo, hi);
     }
 }
 
 // Writes bytes [0, nbytes) of the rate part of the state to dst
 // (nbytes <= RATE), with the widest stores dst's alignment allows.
-template <int RATE>
-__device__ __forceinline__ void squeeze(const uint32_t (&E)[25], const uint32_t (&O)[25], uint8_t *dst,
+template <int RATE, class Rep>
+__device__ __forceinline__ void squeeze(const uint32_t (&A)[25], const uint32_t (&B)[25], uint8_t *dst,
                                         uint32_t nbytes) {
     const uintptr_t d = reinterpret_cast<uintptr_t>(dst);
     if ((d & 15) == 0 && (nbytes & 15) == 0) {
@@ -118,8 +110,8 @@ __device__ __forceinline__ void squeeze(const uint32_t (&E)[25], const uint32_t 
         for (int k = 0; k + 1 < RATE / 8; k += 2) {
             if (uint32_t(8 * k) < nbytes) {
                 uint4 v;
-                from_interleaved(E[k], O[k], v.x, v.y);
-                from_interleaved(E[k + 1], O[k + 1], v.z, v.w);
+                Rep::get_word(A[k], B[k], v.x, v.y);
+                Rep::get_word(A[k + 1], B[k + 1], v.z, v.w);
                 *reinterpret_cast<uint4 *>(dst + 8 * k) = v;
             }
         }
@@ -128,7 +120,7 @@ __device__ __forceinline__ void squeeze(const uint32_t (&E)[25], const uint32_t 
         for (int k = 0; k < RATE / 8; ++k) {
             if (uint32_t(8 * k) < nbytes) {
                 uint2 v;
-                from_interleaved(E[k], O[k], v.x, v.y);
+                Rep::get_word(A[k], B[k], v.x, v.y);
                 *reinterpret_cast<uint2 *>(dst + 8 * k) = v;
             }
         }
@@ -137,7 +129,7 @@ __device__ __forceinline__ void squeeze(const uint32_t (&E)[25], const uint32_t 
         for (int k = 0; k < RATE / 8; ++k) {
             if (uint32_t(8 * k) < nbytes) {
                 uint32_t lo, hi;
-                from_interleaved(E[k], O[k], lo, hi);
+                Rep::get_word(A[k], B[k], lo, hi);
                 *reinterpret_cast<uint32_t *>(dst + 8 * k) = lo;
                 if (uint32_t(8 * k + 4) < nbytes) *reinterpret_cast<uint32_t *>(dst + 8 * k + 4) = hi;
             }
@@ -147,7 +139,7 @@ __device__ __forceinline__ void squeeze(const uint32_t (&E)[25], const uint32_t 
         for (int k = 0; k < RATE / 8; ++k) {
             if (uint32_t(8 * k) < nbytes) {
                 uint32_t lo, hi;
-                from_interleaved(E[k], O[k], lo, hi);
+                Rep::get_word(A[k], B[k], lo, hi);
                 const uint64_t w = (uint64_t(hi) << 32) | lo;
                 const uint32_t nb = nbytes - 8 * k < 8 ? nbytes - 8 * k : 8;
                 for (uint32_t b = 0; b < nb; ++b) dst[8 * k + b] = uint8_t(w >> (8 * b));
@@ -156,74 +148,69 @@ __device__ __forceinline__ void squeeze(const uint32_t (&E)[25], const uint32_t 
     }
 }
 
-// One complete sponge for a message of len bytes at p with variant V's rate,
-// writing dlen output bytes to dst.  The permutation has a single call site,
-// so the unrolled rounds appear once in the code.
-template <int RATE, int DOMAIN, bool A8>
+// One complete sponge for a message of len bytes at p, writing dlen output
+// bytes to dst.  The permutation has a single call site, so its code appears
+// once.
+template <int RATE, int DOMAIN, bool A8, class Rep>
 __device__ __forceinline__ void sponge(const uint8_t *p, uint64_t len, uint8_t *dst, uint32_t dlen) {
-    uint32_t E[25], O[25];
+    uint32_t A[25], B[25];
 #pragma unroll
-    for (int i = 0; i < 25; ++i) E[i] = O[i] = 0;
+    for (int i = 0; i < 25; ++i) A[i] = B[i] = 0;
     const uint64_t nfull = len / RATE;
     const uint32_t rem = uint32_t(len - nfull * RATE);
     const uint32_t nsq = dlen > uint32_t(RATE) ? (dlen - 1) / RATE : 0;  // extra squeeze permutations
     const uint64_t total = nfull + 1 + nsq;
     for (uint64_t i = 0; i < total; ++i) {
-        if (i < nfull) absorb_full<RATE, A8>(E, O, p + i * RATE);
-        else if (i == nfull) absorb_last<RATE, DOMAIN, A8>(E, O, p + nfull * RATE, rem);
-        else squeeze<RATE>(E, O, dst + (i - nfull - 1) * RATE, RATE);
-        keccak_f1600(E, O);
+        if (i < nfull) absorb_full<RATE, A8, Rep>(A, B, p + i * RATE);
+        else if (i == nfull) absorb_last<RATE, DOMAIN, A8, Rep>(A, B, p + nfull * RATE, rem);
+        else squeeze<RATE, Rep>(A, B, dst + (i - nfull - 1) * RATE, RATE);
+        Rep::template permute<false>(A, B);
     }
-    squeeze<RATE>(E, O, dst + uint64_t(nsq) * RATE, dlen - nsq * RATE);
+    squeeze<RATE, Rep>(A, B, dst + uint64_t(nsq) * RATE, dlen - nsq * RATE);
 }
 
 // ---- runtime-rate sponge (ragged batches: the variant varies per message) ----
 
-// Rate and domain byte of a runtime variant (0..5).
-__device__ __forceinline__ int rt_rate(int v) { return variant_rate(v); }
 __device__ __forceinline__ uint32_t rt_domain(int v) { return v < 4 ? 0x06u : 0x1Fu; }
 
 // XORs the first nwords 64-bit words of the block at p into the state.  The
 // loop runs over the largest rate (21 words, SHAKE128) with a predicate, so
 // every state index stays a compile-time register.
-template <bool A8>
-__device__ __forceinline__ void absorb_full_rt(uint32_t (&E)[25], uint32_t (&O)[25], const uint8_t *p,
-                                               int nwords) {
+template <bool A8, class Rep>
+__device__ __forceinline__ void absorb_full_rt(uint32_t (&A)[25], uint32_t (&B)[25], const uint8_t *p, int nwords) {
+    if constexpr (A8) {
 #pragma unroll
-    for (int k = 0; k < 21; ++k) {
-        if (k < nwords) {
-            uint32_t lo, hi;
-            ld_word_a8(p + 8 * k, lo, hi);
-            xor_lane(E[k], O[k], lo, hi);
+        for (int k = 0; k < 21; ++k) {
+            if (k < nwords) {
+                uint32_t lo, hi;
+                ld_word_a8(p + 8 * k, lo, hi);
+                Rep::xor_word(A[k], B[k], lo, hi);
+            }
+        }
+    } else {
+        // 2*nwords aligned 32-bit words cover the block, one more when p is
+        // unaligned; each 64-bit word is two funnel shifts.
+        const uintptr_t start = reinterpret_cast<uintptr_t>(p);
+        const uint32_t *a = reinterpret_cast<const uint32_t *>(start & ~uintptr_t(3));
+        const uint32_t sh = uint32_t(start & 3) * 8;
+        uint32_t prev = __ldg(a);
+#pragma unroll
+        for (int k = 0; k < 21; ++k) {
+            if (k < nwords) {
+                const uint32_t w1 = __ldg(a + 2 * k + 1);
+                const uint32_t w2 = (2 * k + 2 < 2 * nwords || sh != 0) ? __ldg(a + 2 * k + 2) : 0u;
+                const uint32_t lo = __funnelshift_r(prev, w1, sh);
+                const uint32_t hi = __funnelshift_r(w1, w2, sh);
+                prev = w2;
+                Rep::xor_word(A[k], B[k], lo, hi);
+            }
         }
     }
 }
 
-// Same at any alignment: 2*nwords aligned 32-bit words cover the block, one
-// more when p is unaligned; each 64-bit word is two funnel shifts.
-template <>
-__device__ __forceinline__ void absorb_full_rt<false>(uint32_t (&E)[25], uint32_t (&O)[25],
-                                                      const uint8_t *p, int nwords) {
-    const uintptr_t start = reinterpret_cast<uintptr_t>(p);
-    const uint32_t *a = reinterpret_cast<const uint32_t *>(start & ~uintptr_t(3));
-    const uint32_t sh = uint32_t(start & 3) * 8;
-    uint32_t prev = __ldg(a);
-#pragma unroll
-    for (int k = 0; k < 21; ++k) {
-        if (k < nwords) {
-            const uint32_t w1 = __ldg(a + 2 * k + 1);
-            const uint32_t w2 = (2 * k + 2 < 2 * nwords || sh != 0) ? __ldg(a + 2 * k + 2) : 0u;
-            const uint32_t lo = __funnelshift_r(prev, w1, sh);
-            const uint32_t hi = __funnelshift_r(w1, w2, sh);
-            prev = w2;
-            xor_lane(E[k], O[k], lo, hi);
-        }
-    }
-}
-
-template <bool A8>
-__device__ __forceinline__ void absorb_last_rt(uint32_t (&E)[25], uint32_t (&O)[25], const uint8_t *p,
-                                               uint32_t rem, int nwords, uint32_t domain) {
+template <bool A8, class Rep>
+__device__ __forceinline__ void absorb_last_rt(uint32_t (&A)[25], uint32_t (&B)[25], const uint8_t *p, uint32_t rem,
+                                               int nwords, uint32_t domain) {
 #pragma unroll
     for (int k = 0; k < 21; ++k) {
         if (k < nwords) {
@@ -240,37 +227,30 @@ __device__ __forceinline__ void absorb_last_rt(uint32_t (&E)[25], uint32_t (&O)[
                 else hi ^= domain << (sh - 32);
             }
             if (k == nwords - 1) hi ^= 0x80000000u;
-            xor_lane(E[k], O[k], lo, hi);
+            Rep::xor_word(A[k], B[k], lo, hi);
         }
     }
 }
 
-// Writes nbytes (<= 168) of the state's leading bytes to dst.
-__device__ __forceinline__ void squeeze_rt(const uint32_t (&E)[25], const uint32_t (&O)[25], uint8_t *dst,
-                                           uint32_t nbytes) {
-    squeeze<168>(E, O, dst, nbytes);
-}
-
-template <bool A8>
-__device__ __forceinline__ void sponge_rt(const uint8_t *p, uint64_t len, int variant, uint8_t *dst,
-                                          uint32_t dlen) {
-    const int rate = rt_rate(variant);
+template <bool A8, class Rep>
+__device__ __forceinline__ void sponge_rt(const uint8_t *p, uint64_t len, int variant, uint8_t *dst, uint32_t dlen) {
+    const int rate = variant_rate(variant);
     const int nwords = rate / 8;
     const uint32_t domain = rt_domain(variant);
-    uint32_t E[25], O[25];
+    uint32_t A[25], B[25];
 #pragma unroll
-    for (int i = 0; i < 25; ++i) E[i] = O[i] = 0;
+    for (int i = 0; i < 25; ++i) A[i] = B[i] = 0;
     const uint64_t nfull = len / uint64_t(rate);
     const uint32_t rem = uint32_t(len - nfull * uint64_t(rate));
     const uint32_t nsq = dlen > uint32_t(rate) ? (dlen - 1) / uint32_t(rate) : 0;
     const uint64_t total = nfull + 1 + nsq;
     for (uint64_t i = 0; i < total; ++i) {
-        if (i < nfull) absorb_full_rt<A8>(E, O, p + i * rate, nwords);
-        else if (i == nfull) absorb_last_rt<A8>(E, O, p + nfull * rate, rem, nwords, domain);
-        else squeeze_rt(E, O, dst + (i - nfull - 1) * rate, uint32_t(rate));
-        keccak_f1600(E, O);
+        if (i < nfull) absorb_full_rt<A8, Rep>(A, B, p + i * rate, nwords);
+        else if (i == nfull) absorb_last_rt<A8, Rep>(A, B, p + nfull * rate, rem, nwords, domain);
+        else squeeze<168, Rep>(A, B, dst + (i - nfull - 1) * rate, uint32_t(rate));
+        Rep::template permute<false>(A, B);
     }
-    squeeze_rt(E, O, dst + uint64_t(nsq) * rate, dlen - nsq * uint32_t(rate));
+    squeeze<168, Rep>(A, B, dst + uint64_t(nsq) * rate, dlen - nsq * uint32_t(rate));
 }
 
 }  // namespace kb

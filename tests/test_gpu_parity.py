@@ -274,3 +274,15 @@ def test_full_size_merkle_root(cuda_lib, oracle_mod):
         pos += len(nxt)
         level = nxt
     assert root == level[0]
+
+
+def test_interleaved_control_matches_oracle(cuda_lib, oracle_mod):
+    # The bit-interleaved state layout (tuning knob) gives the same digests.
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_REPRESENTATION, cuda_lib.KB_REP_INTERLEAVED)
+    try:
+        for n, L in ((1000, 64), (300, 1000)):
+            msgs = W.uniform_messages(n, L, seed=60 + L)
+            got = gpu_uniform(cuda_lib, msgs, L, L, 1, 32, n)
+            assert np.array_equal(got, oracle_uniform(oracle_mod, msgs, L, L, 1, 32, n)), L
+    finally:
+        cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_REPRESENTATION, cuda_lib.KB_REP_PLAIN)
