@@ -53,7 +53,8 @@ typedef enum {
     KB_ERR_INVALID = -1,  /* bad argument (null pointer, unknown variant, bad size) */
     KB_ERR_NOMEM = -2,    /* internal scratch could not be allocated */
     KB_ERR_CUDA = -3,     /* a CUDA runtime call failed (launch, copy, ...) */
-    KB_ERR_TIMEOUT = -4   /* a bounded device-side wait gave up */
+    KB_ERR_TIMEOUT = -4,  /* a bounded device-side wait gave up */
+    KB_ERR_TOO_LARGE = -5 /* a size beyond a fixed maximum (keccak_batch_noalloc) */
 } kb_status;
 
 /* Bits of the device status word read by keccak_last_error(). */
@@ -102,6 +103,36 @@ int keccak_batch_uniform(const uint8_t *msgs, uint64_t stride, uint64_t len, int
 int keccak_batch(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
                  const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests,
                  uint64_t n, void *stream);
+
+/*
+ * keccak_batch_noalloc -- keccak_batch for callers that cannot allocate
+ * device memory.  The paper has no counterpart: it is a deployment variant of
+ * the ragged batch entry point above.  keccak_batch allocates its scratch (the
+ * digest offsets) with cudaMalloc on first use and whenever a larger batch
+ * arrives; a serving process that reserves all device memory up front, a
+ * plugin or real-time host where cudaMalloc (which can synchronise the whole
+ * device) is not allowed, or code that must know its footprint in advance
+ * cannot accept that.  This entry point runs the same kernels with the scratch
+ * in a fixed device array compiled into the library, of
+ * KB_NOALLOC_MAX_MESSAGES x 8 bytes plus 768 bytes (about 513 KiB), which
+ * every GPU that loads the library holds until the process exits.  It never
+ * calls cudaMalloc or cudaFree.
+ *   Arguments and output layout are those of keccak_batch.
+ *   n > KB_NOALLOC_MAX_MESSAGES returns KB_ERR_TOO_LARGE and does nothing.
+ *   The first call on a device looks up the array's address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before capturing any stream into a CUDA graph.
+ *   All calls share the one array and each call overwrites it: calls whose
+ *   work overlaps on the GPU (several streams or host threads) race, so the
+ *   caller must order them.
+ *   Messages with an invalid variant or SHA3 output size are skipped (their
+ *   outputs left untouched) but, unlike keccak_batch, not reported through
+ *   keccak_last_error.
+ */
+#define KB_NOALLOC_MAX_MESSAGES 65536u
+int keccak_batch_noalloc(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                         const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests,
+                         uint64_t n, void *stream);
 
 /*
  * keccak_batch_uniform_host -- keccak_batch_uniform on HOST buffers, the whole

@@ -19,7 +19,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsha3gb.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "sha3gb.h")
 
-KB_OK, KB_ERR_INVALID, KB_ERR_NOMEM, KB_ERR_CUDA, KB_ERR_TIMEOUT = 0, -1, -2, -3, -4
+KB_OK, KB_ERR_INVALID, KB_ERR_NOMEM, KB_ERR_CUDA, KB_ERR_TIMEOUT, KB_ERR_TOO_LARGE = 0, -1, -2, -3, -4, -5
+KB_NOALLOC_MAX_MESSAGES = 65536
 KB_DEV_BAD_VARIANT, KB_DEV_BAD_OUTLEN, KB_DEV_TIMEOUT = 0x1, 0x2, 0x4
 DIGEST_BYTES = (28, 32, 48, 64, None, None)
 RATE_BYTES = (144, 136, 104, 72, 168, 136)
@@ -47,6 +48,7 @@ _SIGS = {
     "keccak_batch_uniform": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                             ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     "keccak_batch": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_uint64, ctypes.c_void_p]),
+    "keccak_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_uint64, ctypes.c_void_p]),
     "keccak_batch_uniform_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                                  ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
                                                  ctypes.c_void_p]),
@@ -121,6 +123,14 @@ def keccak_batch_uniform(msgs, stride: int, length: int, variant: int, out_len: 
 def keccak_batch(msgs, offsets, lens, variants, out_lens, digests, n: int, stream=None) -> None:
     _check(load().keccak_batch(_ptr(msgs), _ptr(offsets), _ptr(lens), _ptr(variants), _ptr(out_lens),
                                _ptr(digests), n, _stream(stream)), "keccak_batch")
+
+
+def keccak_batch_noalloc(msgs, offsets, lens, variants, out_lens, digests, n: int, stream=None) -> None:
+    """keccak_batch with its scratch in a fixed device array (no device
+    allocation); at most KB_NOALLOC_MAX_MESSAGES messages; calls that overlap
+    on the GPU race."""
+    _check(load().keccak_batch_noalloc(_ptr(msgs), _ptr(offsets), _ptr(lens), _ptr(variants), _ptr(out_lens),
+                                       _ptr(digests), n, _stream(stream)), "keccak_batch_noalloc")
 
 
 def keccak_batch_uniform_host(h_msgs, stride: int, length: int, variant: int, out_len: int, h_digests,
