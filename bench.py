@@ -212,6 +212,8 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--messages", type=int, default=N_MSGS,
                     help="messages per step (default 2^24; smaller only for profiling captures)")
+    ap.add_argument("--ragged-only", type=int, default=0, metavar="N",
+                    help="only run the ragged-batch measurement on N messages (profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -232,6 +234,10 @@ def main() -> None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     binding.load()
+    if args.ragged_only:
+        print(json.dumps(ragged_measurements(binding, workloads, torch, torch.cuda.current_stream(), rank,
+                                             n=args.ragged_only, autotune=False)), flush=True)
+        return
 
     n_msgs = args.messages
     msgs_np = workloads.uniform_messages(n_msgs, MSG_BYTES, seed=1 + rank)
@@ -369,12 +375,68 @@ def extra_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
     out["sha3_256_2p22_x_1KiB_mhash_s"] = n2 / ms / 1e3
     out["sha3_256_2p22_x_1KiB_gb_s"] = n2 * l2 / ms / 1e6
     del m2, d2
+    out["ragged_2p20_loguniform_0_64KiB"] = ragged_measurements(binding, workloads, torch, stream, rank)
     try:
         out["int_lanes_per_sm_clk"] = {name: round(binding.int_issue_probe(op, 4096, stream), 2)
                                        for op, name in enumerate(("lop3", "shf", "prmt", "iadd"))}
     except Exception as e:  # diagnostic only
         out["int_lanes_per_sm_clk"] = f"probe failed: {e}"
     return out
+
+
+RATES = (144, 136, 104, 72, 168, 136)
+
+
+def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, autotune=True) -> dict:
+    """The ragged, mixed-variant batch: 2^20 messages, lengths log-uniform over
+    0..64 KiB, variants uniform over the six functions, SHAKE outputs 16..512 B.
+    Input-order single launch vs the cost-bucketed persistent queue (graph
+    replay), then the queue with the autotuned configuration."""
+    b = workloads.ragged_batch(n, seed=3 + rank, max_len=65536)
+    rates = np.array(RATES, dtype=np.uint64)[b.variants]
+    perms = (b.lens // rates + 1 + np.where(b.out_lens > rates, (b.out_lens.astype(np.uint64) - 1) // rates, 0))
+    total_perms = int(perms.sum())
+    to_dev = lambda a: torch.from_numpy(a.view({8: np.int64, 4: np.int32, 1: np.uint8}[a.itemsize])).cuda()  # noqa
+    d = [to_dev(x) for x in (b.msgs, b.offsets, b.lens, b.variants, b.out_lens)]
+    out = torch.empty(b.total_out(), dtype=torch.uint8, device="cuda")
+    msg_bytes = int(b.lens.sum())
+
+    def timed(reps=3):
+        binding.keccak_batch(*d, out, b.n, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            binding.keccak_batch(*d, out, b.n, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {"messages": b.n, "message_bytes": msg_bytes, "permutations": total_perms}
+    saved = [binding.keccak_tune_get(k) for k in range(6)]
+    try:
+        binding.keccak_tune_set(binding.KB_TUNE_RAGGED_SCHEDULE, binding.KB_SCHEDULE_INPUT_ORDER)
+        ms_in = timed()
+        ref = out.clone()
+        binding.keccak_tune_set(binding.KB_TUNE_RAGGED_SCHEDULE, binding.KB_SCHEDULE_QUEUE)
+        ms_q = timed()
+        same = bool(torch.equal(ref, out))
+        tuned, ms_t = None, None
+        if autotune:
+            tuned = binding.keccak_batch_autotune(*d, out, b.n, stream)
+            ms_t = timed()
+            same = same and bool(torch.equal(ref, out))
+    finally:
+        for k, v in enumerate(saved):
+            binding.keccak_tune_set(k, v)
+    for name, ms in (("input_order", ms_in), ("queue", ms_q), ("queue_autotuned", ms_t)):
+        if ms is None:
+            continue
+        res[name] = {"ms": ms, "mhash_s": b.n / ms / 1e3, "gb_s": msg_bytes / ms / 1e6,
+                     "gperm_s": total_perms / ms / 1e6}
+    res["autotuned_config"] = tuned
+    res["schedules_agree_bytewise"] = same
+    return res
 
 
 def measured_traffic():

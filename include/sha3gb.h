@@ -93,16 +93,33 @@ int keccak_batch_uniform(const uint8_t *msgs, uint64_t stride, uint64_t len, int
  *             digest size for variants 0..3)
  *   digests   device: output i is written at byte exclusive_scan(out_lens)[i]
  *             (outputs packed back to back in message order)
- *   n         number of messages; 0 is a no-op
+ *   n         number of messages, at most 2^32 - 1; 0 is a no-op
  * Per-message errors (a variant outside 0..5, a SHA3-x out_len that is not
  * the digest size) cannot be seen on the host without a sync: those messages
  * are skipped (their output bytes are left untouched) and a bit is set in the
  * device status word (see keccak_last_error).  Uses cached internal scratch
- * of 8 bytes per message plus a small work-queue descriptor.
+ * of 12 bytes per message plus a 4 KiB work-queue descriptor.  The schedule
+ * (KB_TUNE_RAGGED_SCHEDULE) changes only the order of the work, never a byte
+ * of the output.
  */
 int keccak_batch(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
                  const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests,
                  uint64_t n, void *stream);
+
+/*
+ * keccak_batch_autotune -- the autotuner of the ragged schedule: hashes the
+ * given batch (same arguments and outputs as keccak_batch) once per candidate
+ * configuration of the persistent queue kernel (register budget x blocks per
+ * SM), checks that every candidate writes the same bytes as the first, and
+ * records the fastest for this device and this batch size class (n rounded
+ * down to a power of two); later keccak_batch calls of that class use it.
+ * Synchronous.  The chosen register budget, blocks per SM and its time in ms
+ * are written to the HOST pointers when they are not NULL.  Allocates a
+ * temporary device copy of the outputs.
+ */
+int keccak_batch_autotune(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                          const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
+                          void *stream, int64_t *chosen_min_blocks, int64_t *chosen_blocks_per_sm, float *ms);
 
 /*
  * keccak_batch_noalloc -- keccak_batch for callers that cannot allocate
@@ -195,6 +212,28 @@ void keccak_release(void);
 #define KB_TUNE_REPRESENTATION 0
 #define KB_REP_PLAIN 0
 #define KB_REP_INTERLEAVED 1
+/*   KB_TUNE_RAGGED_SCHEDULE: how keccak_batch orders its work --
+ *     KB_SCHEDULE_QUEUE (default: messages sorted into cost buckets, longest
+ *     first, consumed by one persistent launch) or KB_SCHEDULE_INPUT_ORDER (one
+ *     thread per message in input order, the plain one-launch control).
+ *   KB_TUNE_GRAPHS: 1 (default) replays the queue schedule's launches from a
+ *     CUDA graph cached per call signature (pointers, n, stream); 0 launches
+ *     directly.  Work issued on the legacy default stream or on a stream that
+ *     is being captured is always launched directly.
+ *   KB_TUNE_AUTOTUNE: 1 (default) uses configurations found by
+ *     keccak_batch_autotune for batches of the same size class; 0 ignores them.
+ *   KB_TUNE_QUEUE_MIN_BLOCKS: register budget of the queue kernel, as the
+ *     minimum resident 128-thread blocks per SM it is compiled for (4, 5, 6 or
+ *     8; 0 = tuned or default 4).
+ *   KB_TUNE_QUEUE_BLOCKS_PER_SM: blocks per SM of the persistent launch
+ *     (1..32; 0 = tuned or as many as fit). */
+#define KB_TUNE_RAGGED_SCHEDULE 1
+#define KB_SCHEDULE_INPUT_ORDER 0
+#define KB_SCHEDULE_QUEUE 1
+#define KB_TUNE_GRAPHS 2
+#define KB_TUNE_AUTOTUNE 3
+#define KB_TUNE_QUEUE_MIN_BLOCKS 4
+#define KB_TUNE_QUEUE_BLOCKS_PER_SM 5
 int keccak_tune_set(int key, int64_t value);
 int64_t keccak_tune_get(int key);
 

@@ -48,6 +48,9 @@ _SIGS = {
     "keccak_batch_uniform": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                             ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     "keccak_batch": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_uint64, ctypes.c_void_p]),
+    "keccak_batch_autotune": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_uint64, ctypes.c_void_p,
+                                                                      ctypes.c_void_p, ctypes.c_void_p,
+                                                                      ctypes.c_void_p]),
     "keccak_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_uint64, ctypes.c_void_p]),
     "keccak_batch_uniform_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                                  ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
@@ -125,6 +128,16 @@ def keccak_batch(msgs, offsets, lens, variants, out_lens, digests, n: int, strea
                                _ptr(digests), n, _stream(stream)), "keccak_batch")
 
 
+def keccak_batch_autotune(msgs, offsets, lens, variants, out_lens, digests, n: int, stream=None) -> dict:
+    """Runs the ragged-schedule autotuner on this batch (digests are written
+    as by keccak_batch); returns the chosen configuration and its time."""
+    minb, bps, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_float()
+    _check(load().keccak_batch_autotune(_ptr(msgs), _ptr(offsets), _ptr(lens), _ptr(variants), _ptr(out_lens),
+                                        _ptr(digests), n, _stream(stream), ctypes.addressof(minb),
+                                        ctypes.addressof(bps), ctypes.addressof(ms)), "keccak_batch_autotune")
+    return {"min_blocks": minb.value, "blocks_per_sm": bps.value, "ms": ms.value}
+
+
 def keccak_batch_noalloc(msgs, offsets, lens, variants, out_lens, digests, n: int, stream=None) -> None:
     """keccak_batch with its scratch in a fixed device array (no device
     allocation); at most KB_NOALLOC_MAX_MESSAGES messages; calls that overlap
@@ -165,6 +178,9 @@ def keccak_release() -> None:
 
 KB_TUNE_REPRESENTATION = 0
 KB_REP_PLAIN, KB_REP_INTERLEAVED = 0, 1
+KB_TUNE_RAGGED_SCHEDULE, KB_TUNE_GRAPHS, KB_TUNE_AUTOTUNE = 1, 2, 3
+KB_TUNE_QUEUE_MIN_BLOCKS, KB_TUNE_QUEUE_BLOCKS_PER_SM = 4, 5
+KB_SCHEDULE_INPUT_ORDER, KB_SCHEDULE_QUEUE = 0, 1
 
 
 def keccak_tune_set(key: int, value: int) -> None:

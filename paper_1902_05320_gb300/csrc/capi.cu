@@ -107,12 +107,27 @@ int keccak_batch(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *l
                  uint64_t n, void *stream) {
     if (n == 0) return KB_OK;
     if (!msgs || !offsets || !lens || !variant || !out_lens || !digests) return KB_ERR_INVALID;
-    if (n > (UINT64_MAX >> 4)) return KB_ERR_INVALID;
+    if (n > UINT32_MAX) return KB_ERR_INVALID;
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
     return launch_ragged(msgs, offsets, lens, variant, out_lens, digests, n,
                          static_cast<cudaStream_t>(stream), *dev);
+}
+
+int keccak_batch_autotune(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                          const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
+                          void *stream, int64_t *chosen_min_blocks, int64_t *chosen_blocks_per_sm,
+                          float *ms) {
+    if (n == 0) return KB_OK;
+    if (!msgs || !offsets || !lens || !variant || !out_lens || !digests) return KB_ERR_INVALID;
+    if (n > UINT32_MAX) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    return autotune_ragged_queue(msgs, offsets, lens, variant, out_lens, digests, n,
+                                 static_cast<cudaStream_t>(stream), *dev, chosen_min_blocks, chosen_blocks_per_sm,
+                                 ms);
 }
 
 uint64_t merkle_node_count(uint64_t n_leaves) { return merkle_nodes(n_leaves); }
@@ -203,6 +218,9 @@ int keccak_last_error(void *stream) {
 void keccak_release(void) {
     int dev = -1;
     if (cudaGetDevice(&dev) == cudaSuccess) {
+        cudaDeviceSynchronize();
+        release_queue_graphs(dev);
+        forget_tuning(dev);
         std::lock_guard<std::mutex> lk(g_pipe_mu);
         auto it = g_pipes.find(dev);
         if (it != g_pipes.end()) {

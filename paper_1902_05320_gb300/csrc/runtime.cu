@@ -94,8 +94,10 @@ void release_device() {
 }
 
 namespace {
-constexpr int kTuneKeys = 1;
-std::atomic<int64_t> g_tuning[kTuneKeys] = {{KB_REP_PLAIN}};
+constexpr int kTuneKeys = 6;
+// Defaults: plain layout, cost-bucketed queue, graphs on, tuned configs used,
+// register budget and blocks per SM from the tuner (or built-in defaults).
+std::atomic<int64_t> g_tuning[kTuneKeys] = {{KB_REP_PLAIN}, {KB_SCHEDULE_QUEUE}, {1}, {1}, {0}, {0}};
 }  // namespace
 
 int64_t tuning_get(int key) { return (key >= 0 && key < kTuneKeys) ? g_tuning[key].load() : -1; }
@@ -104,6 +106,19 @@ int tuning_set(int key, int64_t value) {
     switch (key) {
         case KB_TUNE_REPRESENTATION:
             if (value != KB_REP_PLAIN && value != KB_REP_INTERLEAVED) return KB_ERR_INVALID;
+            break;
+        case KB_TUNE_RAGGED_SCHEDULE:
+            if (value != KB_SCHEDULE_INPUT_ORDER && value != KB_SCHEDULE_QUEUE) return KB_ERR_INVALID;
+            break;
+        case KB_TUNE_GRAPHS:
+        case KB_TUNE_AUTOTUNE:
+            if (value != 0 && value != 1) return KB_ERR_INVALID;
+            break;
+        case KB_TUNE_QUEUE_MIN_BLOCKS:
+            if (value != 0 && value != 4 && value != 5 && value != 6 && value != 8) return KB_ERR_INVALID;
+            break;
+        case KB_TUNE_QUEUE_BLOCKS_PER_SM:
+            if (value < 0 || value > 32) return KB_ERR_INVALID;
             break;
         default:
             return KB_ERR_INVALID;

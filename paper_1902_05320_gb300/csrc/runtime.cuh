@@ -61,6 +61,15 @@ int launch_ragged_external(const uint8_t *msgs, const uint64_t *offsets, const u
                            uint64_t *out_off, uint64_t *tile_sums, unsigned int *status, int sm_count,
                            cudaStream_t stream);
 uint64_t digest_offsets_tiles(uint64_t n);
+// Cost-bucketed persistent path (sha3_queue.cu).
+int launch_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
+                        const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
+                        const DeviceInfo &dev);
+int autotune_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
+                          const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
+                          const DeviceInfo &dev, int64_t *best_minb, int64_t *best_bps, float *best_ms);
+void release_queue_graphs(int device);
+void forget_tuning(int device);
 uint64_t merkle_nodes(uint64_t n_leaves);
 int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes,
                          cudaStream_t stream, const DeviceInfo &dev);

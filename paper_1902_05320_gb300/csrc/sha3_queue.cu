@@ -1,0 +1,475 @@
+// sha3_queue.cu -- ragged batches in one persistent launch fed by a
+// cost-bucketed work queue (the batch mode of Section 4 for messages of mixed
+// lengths and variants).
+//
+// A message's cost is its number of Keccak-f permutations: floor(len/r) + 1
+// absorbed blocks plus ceil(d/r) - 1 extra squeezes.  Costs fall into 528
+// buckets (exact below 64, eight per octave above).  On the device:
+//   1. k_prep: digest-offset tile sums and a bucket histogram;
+//   2. k_plan: one block scans the tile sums and lays the buckets out
+//      longest-first;
+//   3. k_scatter: digest offsets, and each message's slot in the work order;
+//   4. k_sha3_queue: a grid of (blocks per SM x SMs) blocks; each warp takes
+//      the next 32 entries of the order with one atomic and hashes one
+//      message per thread.  Warps therefore run messages of nearly equal
+//      cost, and the longest messages start first so the tail is short.
+// The five operations (a memset and four kernels) are captured once per call
+// signature into a CUDA graph and replayed afterwards.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <list>
+#include <mutex>
+#include <tuple>
+
+#include "keccak_core.cuh"
+#include "runtime.cuh"
+#include "scan.cuh"
+#include "sponge.cuh"
+
+namespace kb {
+namespace {
+
+constexpr int kBuckets = 528;
+
+// Permutations a message costs (0 for an invalid variant, which the hashing
+// kernel flags and skips).
+__device__ __forceinline__ uint64_t message_cost(uint64_t len, int v, uint32_t dlen) {
+    if (v > 5) return 0;
+    const uint32_t rate = uint32_t(variant_rate(v));
+    return len / rate + 1 + (dlen > rate ? (dlen - 1) / rate : 0);
+}
+
+__device__ __forceinline__ uint32_t cost_bucket(uint64_t c) {
+    if (c < 64) return uint32_t(c);
+    const int e = 63 - __clzll(static_cast<long long>(c));  // >= 6
+    return uint32_t(64 + (e - 6) * 8 + int((c >> (e - 3)) & 7));
+}
+
+struct Control {
+    uint32_t count[kBuckets];   // messages per bucket
+    uint32_t cursor[kBuckets];  // next free slot of each bucket in the order
+    unsigned long long head;    // work-queue position
+};
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_prep(const uint64_t *__restrict__ lens, const uint8_t *__restrict__ variants,
+           const uint32_t *__restrict__ out_lens, uint64_t n, uint64_t *__restrict__ tile_sums, Control *ctl) {
+    __shared__ uint32_t hist[kBuckets];
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const uint64_t base = uint64_t(blockIdx.x) * kScanTile + uint64_t(threadIdx.x) * kScanItems;
+    uint64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const uint64_t i = base + j;
+        if (i < n) {
+            const uint32_t d = out_lens[i];
+            s += d;
+            atomicAdd(&hist[cost_bucket(message_cost(lens[i], variants[i], d))], 1u);
+        }
+    }
+    uint64_t excl;
+    const uint64_t total = block_exclusive_scan(s, excl);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+    __syncthreads();
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x)
+        if (hist[b]) atomicAdd(&ctl->count[b], hist[b]);
+}
+
+// One block: exclusive scan of the tile sums, and bucket starts in
+// descending cost order (bucket kBuckets-1 first).
+__global__ void __launch_bounds__(kScanThreads) k_plan(uint64_t *tile_sums, uint64_t ntiles, Control *ctl) {
+    uint64_t carry = 0;
+    for (uint64_t start = 0; start < ntiles; start += kScanThreads) {
+        const uint64_t i = start + threadIdx.x;
+        const uint64_t v = i < ntiles ? tile_sums[i] : 0;
+        uint64_t excl;
+        const uint64_t total = block_exclusive_scan(v, excl);
+        if (i < ntiles) tile_sums[i] = carry + excl;
+        carry += total;
+    }
+    carry = 0;
+    for (int start = 0; start < kBuckets; start += kScanThreads) {
+        const int t = start + int(threadIdx.x);
+        const int b = kBuckets - 1 - t;
+        const uint64_t v = t < kBuckets ? ctl->count[b] : 0;
+        uint64_t excl;
+        const uint64_t total = block_exclusive_scan(v, excl);
+        if (t < kBuckets) ctl->cursor[b] = uint32_t(carry + excl);
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_scatter(const uint64_t *__restrict__ lens, const uint8_t *__restrict__ variants,
+              const uint32_t *__restrict__ out_lens, uint64_t n, const uint64_t *__restrict__ tile_sums,
+              uint64_t *__restrict__ out_off, uint32_t *__restrict__ order, Control *ctl) {
+    __shared__ uint32_t hist[kBuckets];
+    __shared__ uint32_t start[kBuckets];
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const uint64_t base = uint64_t(blockIdx.x) * kScanTile + uint64_t(threadIdx.x) * kScanItems;
+    uint32_t d[kScanItems], key[kScanItems], rank[kScanItems];
+    uint64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const uint64_t i = base + j;
+        d[j] = 0;
+        key[j] = 0;
+        rank[j] = 0;
+        if (i < n) {
+            d[j] = out_lens[i];
+            key[j] = cost_bucket(message_cost(lens[i], variants[i], d[j]));
+            rank[j] = atomicAdd(&hist[key[j]], 1u);
+        }
+        s += d[j];
+    }
+    uint64_t excl;
+    block_exclusive_scan(s, excl);
+    uint64_t acc = tile_sums[blockIdx.x] + excl;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < n) out_off[base + j] = acc;
+        acc += d[j];
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x)
+        start[b] = hist[b] ? atomicAdd(&ctl->cursor[b], hist[b]) : 0u;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (base + j < n) order[start[key[j]] + rank[j]] = uint32_t(base + j);
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
+    k_sha3_queue(const uint8_t *__restrict__ msgs, const uint64_t *__restrict__ offsets,
+                 const uint64_t *__restrict__ lens, const uint8_t *__restrict__ variants,
+                 const uint32_t *__restrict__ out_lens, const uint64_t *__restrict__ out_off,
+                 const uint32_t *__restrict__ order, uint8_t *__restrict__ digests, uint64_t n, Control *ctl,
+                 unsigned int *status) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->head, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+        const uint64_t idx = base + lane;
+        if (idx < n) hash_ragged_message(msgs, offsets, lens, variants, out_lens, out_off, digests, order[idx], status);
+    }
+}
+
+// Register budgets the tuner can choose (minimum resident blocks of 128
+// threads per SM, which caps registers per thread at 65536 / (128 x MINB)).
+const int kMinBlocksChoices[] = {4, 5, 6, 8};
+
+const void *queue_kernel(int minb) {
+    switch (minb) {
+        case 5: return reinterpret_cast<const void *>(&k_sha3_queue<5>);
+        case 6: return reinterpret_cast<const void *>(&k_sha3_queue<6>);
+        case 8: return reinterpret_cast<const void *>(&k_sha3_queue<8>);
+        default: return reinterpret_cast<const void *>(&k_sha3_queue<4>);
+    }
+}
+
+struct QueueConfig {
+    int minb = 4;           // register budget (template instance)
+    int blocks_per_sm = 0;  // 0: as many as fit
+};
+
+struct Buffers {
+    uint64_t *out_off;
+    uint64_t *tile_sums;
+    uint32_t *order;
+    Control *ctl;
+};
+
+size_t scratch_bytes(uint64_t n, uint64_t ntiles) {
+    const size_t a = 8 * n, b = 8 * ntiles, c = (4 * n + 255) / 256 * 256;
+    return 256 + a + b + c + sizeof(Control);
+}
+
+Buffers carve(uint8_t *scratch, uint64_t n, uint64_t ntiles) {
+    Buffers bf;
+    bf.ctl = reinterpret_cast<Control *>(scratch);
+    uint8_t *p = scratch + (sizeof(Control) + 255) / 256 * 256;
+    bf.out_off = reinterpret_cast<uint64_t *>(p);
+    bf.tile_sums = bf.out_off + n;
+    bf.order = reinterpret_cast<uint32_t *>(bf.tile_sums + ntiles);
+    return bf;
+}
+
+uint64_t queue_grid(const QueueConfig &cfg, uint64_t n, const DeviceInfo &dev) {
+    uint64_t grid = persistent_grid(queue_kernel(cfg.minb), kThreads, 0, (n + 31) / 32 * 32, dev);
+    if (cfg.blocks_per_sm > 0) grid = std::min<uint64_t>(grid, uint64_t(cfg.blocks_per_sm) * dev.sm_count);
+    return grid;
+}
+
+// Enqueues the whole ragged pipeline on `stream` (capturable: no allocation,
+// no synchronisation, no occupancy queries).
+int issue(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
+          const uint32_t *out_lens, uint8_t *digests, uint64_t n, const Buffers &bf, uint64_t ntiles,
+          const QueueConfig &cfg, uint64_t grid, cudaStream_t stream, const DeviceInfo &dev) {
+    if (cudaMemsetAsync(bf.ctl, 0, sizeof(Control), stream) != cudaSuccess) return KB_ERR_CUDA;
+    k_prep<<<unsigned(ntiles), kScanThreads, 0, stream>>>(lens, variants, out_lens, n, bf.tile_sums, bf.ctl);
+    k_plan<<<1, kScanThreads, 0, stream>>>(bf.tile_sums, ntiles, bf.ctl);
+    k_scatter<<<unsigned(ntiles), kScanThreads, 0, stream>>>(lens, variants, out_lens, n, bf.tile_sums, bf.out_off,
+                                                             bf.order, bf.ctl);
+    const void *fn = queue_kernel(cfg.minb);
+    void *args[] = {&msgs, &offsets, &lens, &variants, &out_lens, const_cast<uint64_t **>(&bf.out_off),
+                    const_cast<uint32_t **>(&bf.order), &digests, &n, const_cast<Control **>(&bf.ctl),
+                    const_cast<unsigned int **>(&dev.d_status)};
+    if (cudaLaunchKernel(fn, dim3(unsigned(grid)), dim3(kThreads), args, 0, stream) != cudaSuccess)
+        return KB_ERR_CUDA;
+    return cuda_status(cudaGetLastError());
+}
+
+// ---- graph cache --------------------------------------------------------------
+
+struct GraphKey {
+    const void *ptrs[7];
+    uint64_t n;
+    cudaStream_t stream;
+    int minb, blocks_per_sm, device;
+    bool operator==(const GraphKey &o) const {
+        return std::memcmp(ptrs, o.ptrs, sizeof ptrs) == 0 && n == o.n && stream == o.stream && minb == o.minb &&
+               blocks_per_sm == o.blocks_per_sm && device == o.device;
+    }
+};
+
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec;
+};
+
+constexpr size_t kGraphCacheSize = 16;
+std::mutex g_graph_mu;
+std::list<GraphEntry> g_graphs;  // most recently used first
+
+void drop_graphs_locked(int device) {
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+        if (device < 0 || it->key.device == device) {
+            cudaGraphExecDestroy(it->exec);
+            it = g_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// ---- tuned configurations -------------------------------------------------------
+
+std::mutex g_tune_mu;
+struct TuneEntry {
+    int device;
+    int size_class;
+    QueueConfig cfg;
+};
+std::list<TuneEntry> g_tuned;
+
+int size_class(uint64_t n) { return n ? 63 - __builtin_clzll(n) : 0; }
+
+QueueConfig choose_config(uint64_t n, const DeviceInfo &dev) {
+    QueueConfig cfg;
+    const int64_t regs = tuning_get(KB_TUNE_QUEUE_MIN_BLOCKS);
+    const int64_t bps = tuning_get(KB_TUNE_QUEUE_BLOCKS_PER_SM);
+    if (tuning_get(KB_TUNE_AUTOTUNE) != 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto &t : g_tuned)
+            if (t.device == dev.device && t.size_class == size_class(n)) {
+                cfg = t.cfg;
+                break;
+            }
+    }
+    if (regs > 0) cfg.minb = int(regs);
+    if (bps > 0) cfg.blocks_per_sm = int(bps);
+    return cfg;
+}
+
+}  // namespace
+
+void release_queue_graphs(int device) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    drop_graphs_locked(device);
+}
+
+int launch_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
+                        const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
+                        const DeviceInfo &dev) {
+    const uint64_t ntiles = digest_offsets_tiles(n);
+    int err = KB_OK;
+    const size_t bytes = scratch_bytes(n, ntiles);
+    uint8_t *scratch = static_cast<uint8_t *>(stream_scratch(stream, bytes, &err));
+    if (!scratch) return err;
+    const Buffers bf = carve(scratch, n, ntiles);
+    const QueueConfig cfg = choose_config(n, dev);
+    const uint64_t grid = queue_grid(cfg, n, dev);
+
+    // Graph replay needs a capturable stream that is not already capturing.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool graphs = tuning_get(KB_TUNE_GRAPHS) != 0 && stream != nullptr &&
+                        cudaStreamIsCapturing(stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+    if (!graphs) return issue(msgs, offsets, lens, variants, out_lens, digests, n, bf, ntiles, cfg, grid, stream, dev);
+
+    GraphKey key{{msgs, offsets, lens, variants, out_lens, digests, scratch}, n, stream, cfg.minb,
+                 cfg.blocks_per_sm, dev.device};
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+            if (it->key == key) {
+                g_graphs.splice(g_graphs.begin(), g_graphs, it);
+                return cuda_status(cudaGraphLaunch(it->exec, stream));
+            }
+        }
+    }
+    // Capture once, instantiate, launch.
+    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return issue(msgs, offsets, lens, variants, out_lens, digests, n, bf, ntiles, cfg, grid, stream, dev);
+    }
+    const int rc = issue(msgs, offsets, lens, variants, out_lens, digests, n, bf, ntiles, cfg, grid, stream, dev);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t end = cudaStreamEndCapture(stream, &graph);
+    if (rc != KB_OK || end != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != KB_OK ? rc : KB_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t inst = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (inst != cudaSuccess) {
+        cudaGetLastError();
+        return issue(msgs, offsets, lens, variants, out_lens, digests, n, bf, ntiles, cfg, grid, stream, dev);
+    }
+    const int launched = cuda_status(cudaGraphLaunch(exec, stream));
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    g_graphs.push_front(GraphEntry{key, exec});
+    while (g_graphs.size() > kGraphCacheSize) {
+        cudaGraphExecDestroy(g_graphs.back().exec);
+        g_graphs.pop_back();
+    }
+    return launched;
+}
+
+__global__ void k_compare(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b, uint64_t bytes,
+                          unsigned int *mismatch) {
+    const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < bytes; i += step)
+        if (a[i] != b[i]) {
+            atomicOr(mismatch, 1u);
+            return;
+        }
+}
+
+// Autotuner: times every (register budget, blocks per SM) candidate on this
+// batch, checks that each writes the same bytes as the first, and keeps the
+// fastest for batches of the same size class on this device.  Synchronous;
+// allocates a reference copy of the outputs for the duration of the call.
+int autotune_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
+                          const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
+                          const DeviceInfo &dev, int64_t *best_minb, int64_t *best_bps, float *best_ms) {
+    const uint64_t ntiles = digest_offsets_tiles(n);
+    int err = KB_OK;
+    const size_t bytes = scratch_bytes(n, ntiles);
+    uint8_t *scratch = static_cast<uint8_t *>(stream_scratch(stream, bytes, &err));
+    if (!scratch) return err;
+    const Buffers bf = carve(scratch, n, ntiles);
+    cudaEvent_t a = nullptr, b = nullptr;
+    uint8_t *ref = nullptr;
+    unsigned int *mismatch = nullptr;
+    uint64_t total_out = 0;
+    QueueConfig best;
+    float best_t = 1e30f;
+    int rc = KB_OK;
+    bool have_ref = false;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess ||
+        cudaMalloc(&mismatch, sizeof(unsigned int)) != cudaSuccess)
+        rc = KB_ERR_CUDA;
+    for (int minb : kMinBlocksChoices) {
+        if (rc != KB_OK) break;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel(minb), kThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        for (int bps = per_sm; bps >= 1 && bps >= per_sm - 2 && rc == KB_OK; --bps) {
+            QueueConfig cfg;
+            cfg.minb = minb;
+            cfg.blocks_per_sm = bps;
+            const uint64_t grid = queue_grid(cfg, n, dev);
+            // One untimed run, then the timed one.
+            rc = issue(msgs, offsets, lens, variants, out_lens, digests, n, bf, ntiles, cfg, grid, stream, dev);
+            if (rc == KB_OK) rc = cuda_status(cudaEventRecord(a, stream));
+            if (rc == KB_OK) rc = issue(msgs, offsets, lens, variants, out_lens, digests, n, bf, ntiles, cfg, grid, stream, dev);
+            if (rc == KB_OK) rc = cuda_status(cudaEventRecord(b, stream));
+            if (rc == KB_OK) rc = cuda_status(cudaEventSynchronize(b));
+            float ms = 0;
+            if (rc == KB_OK) rc = cuda_status(cudaEventElapsedTime(&ms, a, b));
+            if (rc != KB_OK) break;
+            if (!have_ref) {
+                // Output size: last digest offset + its length.
+                uint64_t last_off = 0;
+                uint32_t last_len = 0;
+                if (cudaMemcpy(&last_off, bf.out_off + (n - 1), 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                    cudaMemcpy(&last_len, out_lens + (n - 1), 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                    rc = KB_ERR_CUDA;
+                    break;
+                }
+                total_out = last_off + last_len;
+                if (total_out && cudaMalloc(&ref, total_out) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = KB_ERR_NOMEM;
+                    break;
+                }
+                if (total_out && cudaMemcpyAsync(ref, digests, total_out, cudaMemcpyDeviceToDevice, stream) != cudaSuccess) {
+                    rc = KB_ERR_CUDA;
+                    break;
+                }
+                have_ref = true;
+            } else if (total_out) {
+                unsigned int bad = 0;
+                if (cudaMemsetAsync(mismatch, 0, sizeof bad, stream) != cudaSuccess) { rc = KB_ERR_CUDA; break; }
+                k_compare<<<dev.sm_count * 8, 256, 0, stream>>>(ref, digests, total_out, mismatch);
+                if (cudaMemcpyAsync(&bad, mismatch, sizeof bad, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+                    cudaStreamSynchronize(stream) != cudaSuccess) {
+                    rc = KB_ERR_CUDA;
+                    break;
+                }
+                if (bad) continue;  // a configuration that changes the output is never chosen
+            }
+            if (ms < best_t) {
+                best_t = ms;
+                best = cfg;
+            }
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (ref) cudaFree(ref);
+    if (mismatch) cudaFree(mismatch);
+    if (rc != KB_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto it = g_tuned.begin(); it != g_tuned.end();)
+            it = (it->device == dev.device && it->size_class == size_class(n)) ? g_tuned.erase(it) : std::next(it);
+        g_tuned.push_front(TuneEntry{dev.device, size_class(n), best});
+    }
+    // Leave the caller's digests from the chosen configuration.
+    rc = issue(msgs, offsets, lens, variants, out_lens, digests, n, bf, ntiles, best, queue_grid(best, n, dev), stream,
+               dev);
+    if (best_minb) *best_minb = best.minb;
+    if (best_bps) *best_bps = best.blocks_per_sm;
+    if (best_ms) *best_ms = best_t;
+    return rc;
+}
+
+void forget_tuning(int device) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto it = g_tuned.begin(); it != g_tuned.end();)
+        it = (device < 0 || it->device == device) ? g_tuned.erase(it) : std::next(it);
+}
+
+}  // namespace kb

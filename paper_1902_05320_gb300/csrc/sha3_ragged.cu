@@ -2,51 +2,20 @@
 // the six variants in one call (the batch mode of Section 4 with the paper's
 // equal-length restriction of Section 4.3 lifted).
 //
-// Steps on the device, all on the caller's stream:
-//   1. digest offsets: exclusive prefix sum of out_lens (three small kernels);
-//   2. one thread per message: the runtime-rate sponge of sponge.cuh.
+// Two schedules, chosen by KB_TUNE_RAGGED_SCHEDULE:
+//  * the cost-bucketed persistent work queue of sha3_queue.cu (default);
+//  * input order, kept as the plain one-launch control: digest offsets by an
+//    exclusive prefix sum of out_lens (three small kernels), then one thread
+//    per message in a grid-stride loop.
 #include <cuda_runtime.h>
 
 #include "keccak_core.cuh"
 #include "runtime.cuh"
+#include "scan.cuh"
 #include "sponge.cuh"
 
 namespace kb {
 namespace {
-
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
-
-// Block-wide exclusive scan of one value per thread; returns the block total.
-__device__ uint64_t block_exclusive_scan(uint64_t v, uint64_t &excl) {
-    __shared__ uint64_t warp_sums[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        uint64_t s = lane < nw ? warp_sums[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
-        }
-        if (lane < nw) warp_sums[lane] = s;
-    }
-    __syncthreads();
-    const uint64_t before = warp ? warp_sums[warp - 1] : 0;
-    const uint64_t total = warp_sums[(blockDim.x >> 5) - 1];
-    excl = before + x - v;
-    __syncthreads();
-    return total;
-}
 
 __global__ void __launch_bounds__(kScanThreads) k_tile_sums(const uint32_t *__restrict__ out_lens, uint64_t n,
                                                             uint64_t *__restrict__ tile_sums) {
@@ -101,19 +70,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
                   const uint32_t *__restrict__ out_lens, const uint64_t *__restrict__ out_off,
                   uint8_t *__restrict__ digests, uint64_t n, unsigned int *status) {
     const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += step) {
-        const int v = variants[i];
-        const uint32_t dlen = out_lens[i];
-        if (v > 5) {
-            atomicOr(status, KB_DEV_BAD_VARIANT);
-            continue;
-        }
-        if (v < 4 && dlen != uint32_t(variant_digest(v))) {
-            atomicOr(status, KB_DEV_BAD_OUTLEN);
-            continue;
-        }
-        sponge_rt<false, PlainRep>(msgs + offsets[i], lens[i], v, digests + out_off[i], dlen);
-    }
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += step)
+        hash_ragged_message(msgs, offsets, lens, variants, out_lens, out_off, digests, i, status);
 }
 
 }  // namespace
@@ -132,6 +90,9 @@ uint64_t digest_offsets_tiles(uint64_t n) { return (n + kScanTile - 1) / kScanTi
 int launch_ragged(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
                   const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
                   const DeviceInfo &dev) {
+    if (tuning_get(KB_TUNE_RAGGED_SCHEDULE) == KB_SCHEDULE_QUEUE)
+        return launch_ragged_queue(msgs, offsets, lens, variants, out_lens, digests, n, stream, dev);
+    // Input order: one thread per message, grid-stride.
     const uint64_t ntiles = digest_offsets_tiles(n);
     int err = KB_OK;
     uint8_t *scratch = static_cast<uint8_t *>(stream_scratch(stream, size_t(8 * (n + ntiles)), &err));

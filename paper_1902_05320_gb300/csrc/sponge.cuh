@@ -15,6 +15,7 @@
 
 #include <cstdint>
 
+#include "../../include/sha3gb.h"
 #include "keccak_core.cuh"
 
 namespace kb {
@@ -251,6 +252,25 @@ __device__ __forceinline__ void sponge_rt(const uint8_t *p, uint64_t len, int va
         Rep::template permute<false>(A, B);
     }
     squeeze<168, Rep>(A, B, dst + uint64_t(nsq) * rate, dlen - nsq * uint32_t(rate));
+}
+
+// One message of a ragged batch: checks its descriptor, then hashes it.
+// Bad descriptors set a bit in *status and leave the output untouched.
+__device__ __forceinline__ void hash_ragged_message(const uint8_t *msgs, const uint64_t *offsets,
+                                                    const uint64_t *lens, const uint8_t *variants,
+                                                    const uint32_t *out_lens, const uint64_t *out_off,
+                                                    uint8_t *digests, uint64_t i, unsigned int *status) {
+    const int v = variants[i];
+    const uint32_t dlen = out_lens[i];
+    if (v > 5) {
+        atomicOr(status, KB_DEV_BAD_VARIANT);
+        return;
+    }
+    if (v < 4 && dlen != uint32_t(variant_digest(v))) {
+        atomicOr(status, KB_DEV_BAD_OUTLEN);
+        return;
+    }
+    sponge_rt<false, PlainRep>(msgs + offsets[i], lens[i], v, digests + out_off[i], dlen);
 }
 
 }  // namespace kb

@@ -58,3 +58,19 @@ def test_argument_errors_are_returned_before_any_cuda_call(lib):
 def test_merkle_node_count(lib, oracle_mod):
     for n in (0, 1, 2, 3, 5, 7, 8, 9, 1000, 524288):
         assert binding.merkle_node_count(n) == oracle_mod.merkle_node_count(n)
+
+
+def test_tuning_knobs_validate_values(lib):
+    keys = range(6)
+    saved = [binding.keccak_tune_get(k) for k in keys]
+    try:
+        assert saved[0] == binding.KB_REP_PLAIN and saved[1] == binding.KB_SCHEDULE_QUEUE
+        for key, bad in ((0, 2), (1, 5), (2, 3), (3, -1), (4, 7), (5, 33), (99, 0)):
+            assert lib.keccak_tune_set(key, bad) == binding.KB_ERR_INVALID
+        assert binding.keccak_tune_get(99) == -1
+        for key, good in ((0, 1), (1, 0), (2, 0), (3, 0), (4, 6), (5, 3)):
+            binding.keccak_tune_set(key, good)
+            assert binding.keccak_tune_get(key) == good
+    finally:
+        for k, v in zip(keys, saved):
+            binding.keccak_tune_set(k, v)

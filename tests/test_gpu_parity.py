@@ -286,3 +286,66 @@ def test_interleaved_control_matches_oracle(cuda_lib, oracle_mod):
             assert np.array_equal(got, oracle_uniform(oracle_mod, msgs, L, L, 1, 32, n)), L
     finally:
         cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_REPRESENTATION, cuda_lib.KB_REP_PLAIN)
+
+
+# -- ragged schedules, graph replay, autotuner -------------------------------------------
+@pytest.fixture
+def restore_tuning(cuda_lib):
+    keys = range(6)
+    saved = [cuda_lib.keccak_tune_get(k) for k in keys]
+    yield
+    for k, v in zip(keys, saved):
+        cuda_lib.keccak_tune_set(k, v)
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_ragged_schedules_match_oracle(cuda_lib, oracle_mod, restore_tuning, schedule, graphs):
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_RAGGED_SCHEDULE, schedule)
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_GRAPHS, graphs)
+    b = W.ragged_batch(5000, seed=70 + schedule, max_len=5000, gap=4)
+    want = _oracle_ragged(oracle_mod, b)
+    assert np.array_equal(_run_ragged(cuda_lib, b), want)
+    assert cuda_lib.keccak_last_error() == 0
+
+
+@pytest.mark.parametrize("min_blocks", [4, 5, 6, 8])
+def test_queue_register_budgets_match_oracle(cuda_lib, oracle_mod, restore_tuning, min_blocks):
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_QUEUE_MIN_BLOCKS, min_blocks)
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_QUEUE_BLOCKS_PER_SM, 2)
+    b = W.ragged_batch(1500, seed=80 + min_blocks, max_len=2000, gap=2)
+    assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
+
+
+def test_graph_replay_reads_current_bytes(cuda_lib, oracle_mod, restore_tuning):
+    # A replayed graph holds pointers, not contents: new bytes in the same
+    # buffers give the new digests, on a non-default stream.
+    torch = _torch()
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_GRAPHS, 1)
+    b = W.ragged_batch(2000, seed=90, max_len=3000, gap=1)
+    s = torch.cuda.Stream()
+    d = [dev(x) for x in (b.msgs, b.offsets, b.lens, b.variants, b.out_lens)]
+    out = torch.zeros(b.total_out(), dtype=torch.uint8, device="cuda")
+    for trial in range(3):
+        fresh = W.random_bytes(b.msgs.size, seed=1000 + trial)
+        d[0].copy_(torch.from_numpy(fresh))
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            cuda_lib.keccak_batch(*d, out, b.n, s)
+        s.synchronize()
+        want = oracle_mod.hash_batch(fresh, b.offsets, b.lens, b.variants, b.out_lens, THREADS)
+        assert np.array_equal(out.cpu().numpy(), want), trial
+
+
+def test_autotune_keeps_digests(cuda_lib, oracle_mod, restore_tuning):
+    torch = _torch()
+    b = W.ragged_batch(3000, seed=95, max_len=8000, gap=3)
+    d = [dev(x) for x in (b.msgs, b.offsets, b.lens, b.variants, b.out_lens)]
+    out = torch.zeros(b.total_out(), dtype=torch.uint8, device="cuda")
+    chosen = cuda_lib.keccak_batch_autotune(*d, out, b.n)
+    assert chosen["min_blocks"] in (4, 5, 6, 8) and chosen["blocks_per_sm"] >= 1 and chosen["ms"] > 0
+    want = _oracle_ragged(oracle_mod, b)
+    assert np.array_equal(host(out)[: b.total_out()], want)
+    out.zero_()
+    cuda_lib.keccak_batch(*d, out, b.n)  # now runs with the tuned configuration
+    assert np.array_equal(host(out)[: b.total_out()], want)
