@@ -462,8 +462,7 @@ def csrc_digest() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1902_05320_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")) and name in ("keccak_core.cuh", "sponge.cuh", "sha3_uniform.cu",
-                                                       "runtime.cuh"):
+        if name in ("keccak_core.cuh", "keccak_interleaved.cuh", "sponge.cuh", "sha3_uniform.cu", "runtime.cuh"):
             h.update(name.encode())
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
