@@ -212,6 +212,8 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--messages", type=int, default=N_MSGS,
                     help="messages per step (default 2^24; smaller only for profiling captures)")
+    ap.add_argument("--serving-only", type=float, default=0.0, metavar="SECONDS",
+                    help="only run the serving measurement for SECONDS of arrivals")
     ap.add_argument("--ragged-only", type=int, default=0, metavar="N",
                     help="only run the ragged-batch measurement on N messages (profiling captures)")
     args = ap.parse_args()
@@ -234,6 +236,9 @@ def main() -> None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     binding.load()
+    if args.serving_only:
+        print(json.dumps(serving_measurements(workloads, torch, rank, seconds=args.serving_only)), flush=True)
+        return
     if args.ragged_only:
         print(json.dumps(ragged_measurements(binding, workloads, torch, torch.cuda.current_stream(), rank,
                                              n=args.ragged_only, autotune=False)), flush=True)
@@ -376,6 +381,8 @@ def extra_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
     out["sha3_256_2p22_x_1KiB_gb_s"] = n2 * l2 / ms / 1e6
     del m2, d2
     out["ragged_2p20_loguniform_0_64KiB"] = ragged_measurements(binding, workloads, torch, stream, rank)
+    out["serving_poisson_200k_rps_10s"] = serving_measurements(workloads, torch, rank)
+    out["merkle_4GiB_8KiB_leaves"] = merkle_measurements(binding, workloads, torch, stream, rank)
     try:
         out["int_lanes_per_sm_clk"] = {name: round(binding.int_issue_probe(op, 4096, stream), 2)
                                        for op, name in enumerate(("lop3", "shf", "prmt", "iadd"))}
@@ -436,6 +443,62 @@ def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, auto
                      "gperm_s": total_perms / ms / 1e6}
     res["autotuned_config"] = tuned
     res["schedules_agree_bytewise"] = same
+    return res
+
+
+def merkle_measurements(binding, workloads, torch, stream, rank, n_leaves=1 << 19, leaf_bytes=8192) -> dict:
+    """Tree mode: 4 GiB of random bytes in 8 KiB leaves up to the root."""
+    buf = torch.from_numpy(workloads.merkle_buffer(n_leaves, leaf_bytes, seed=4 + rank)).cuda()
+    nodes = torch.empty(32 * binding.merkle_node_count(n_leaves), dtype=torch.uint8, device="cuda")
+
+    def run():
+        binding.merkle_sha3_256_levels(buf, n_leaves, leaf_bytes, nodes, stream)
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    perms = n_leaves * ((leaf_bytes + 1) // 136 + 1) + (binding.merkle_node_count(n_leaves) - n_leaves)
+    t = time.perf_counter()
+    root = binding.merkle_sha3_256(buf, n_leaves, leaf_bytes, stream)
+    root_ms = (time.perf_counter() - t) * 1e3
+    hbm_bytes = n_leaves * leaf_bytes + 32 * binding.merkle_node_count(n_leaves) * 2
+    return {"leaves": n_leaves, "leaf_bytes": leaf_bytes, "ms": ms, "root_call_ms": root_ms,
+            "gb_s": n_leaves * leaf_bytes / ms / 1e6, "gperm_s": perms / ms / 1e6,
+            "hbm_frac_of_measured": hbm_bytes / ms / 1e6 / 6699.8, "root": root.hex()}
+
+
+def serving_measurements(workloads, torch, rank, rate=200_000, seconds=10.0) -> dict:
+    """The serving loop: Poisson arrivals at `rate` requests/s for `seconds`,
+    messages log-uniform 32 B..1 MiB from a 4 GiB pinned pool, variants mixed,
+    admitted against a 2 GiB device budget."""
+    from paper_1902_05320_gb300.serve import Server
+
+    wl = workloads.serving_workload(rate, seconds, seed=5 + rank, pool_bytes=4 << 30)
+    pool = torch.empty(wl.pool.size, dtype=torch.uint8, pin_memory=True)
+    pool.copy_(torch.from_numpy(wl.pool))
+    total = int(wl.out_lens.sum(dtype=np.uint64))
+    outputs = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+    lat = np.zeros(wl.n, dtype=np.int64)
+    with Server(hbm_budget_bytes=2 << 30, max_inflight=16, max_batch_requests=4096) as srv:
+        st = srv.replay(pool, wl.offsets, wl.lens, wl.variants, wl.out_lens, wl.arrival_ns, outputs, lat)
+    offered_bytes = int(wl.lens.sum())
+    big = wl.lens >= (512 << 10)
+    res = {"requests": wl.n, "offered_rps": rate, "offered_gb_s": offered_bytes / seconds / 1e9,
+           "throughput_rps": st["throughput_rps"], "throughput_gb_s": st["throughput_gbs"],
+           "p50_us": st["lat_p50_us"], "p90_us": st["lat_p90_us"], "p99_us": st["lat_p99_us"],
+           "p999_us": st["lat_p999_us"], "max_us": st["lat_max_us"], "mean_us": st["lat_mean_us"],
+           "batches": st["batches"], "max_batch_requests_seen": st["max_batch_requests_seen"],
+           "peak_arena_bytes": st["peak_arena_bytes"], "per_request_completion": bool(st["completion_ring"]),
+           "p50_us_small_lt_4KiB": float(np.percentile(lat[wl.lens < 4096], 50) / 1e3),
+           "p99_us_small_lt_4KiB": float(np.percentile(lat[wl.lens < 4096], 99) / 1e3),
+           "p50_us_large_ge_512KiB": float(np.percentile(lat[big], 50) / 1e3) if big.any() else None}
     return res
 
 

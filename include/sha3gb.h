@@ -190,6 +190,88 @@ uint64_t merkle_node_count(uint64_t n_leaves);
 int merkle_sha3_256_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes,
                            uint8_t *nodes, void *stream);
 
+/*
+ * Serving loop (continuous batching).  A server owns one device arena of
+ * hbm_budget_bytes -- the admission budget: a request enters a batch only when
+ * its message fits in the arena's free space, and its bytes stay resident
+ * there while it is hashed.  Requests travel in two lanes by cost (number of
+ * Keccak-f permutations): short requests get an eighth of the arena and
+ * max_inflight streams of their own, so they never wait behind the long
+ * sequential chains of large messages, which use the rest.  Whenever a lane
+ * has a free stream and waiting requests, the server forms a batch of them
+ * (oldest first, at most max_batch_requests and max_batch_bytes),
+ * copies their messages into the arena, hashes them longest first and writes
+ * each output directly to its host buffer; requests that arrive meanwhile go
+ * into the next batches, which run concurrently on other streams.  Each
+ * request completes as soon as its own output is written (through a
+ * completion ring in host memory when the device supports native host
+ * atomics, otherwise with its batch).  The paper has no serving loop; this is
+ * the batch mode of Section 4 fed continuously.
+ *
+ * Message and output buffers are HOST memory that the device can access
+ * (page-locked: cudaHostAlloc / cudaHostRegister, or torch pin_memory); they
+ * must stay valid until the request completes.
+ */
+typedef struct kb_server kb_server;
+
+typedef struct {
+    uint64_t hbm_budget_bytes;     /* device arena size (>= 4096) */
+    uint32_t max_inflight;         /* batches in flight at once per lane, 1..64 */
+    uint32_t max_batch_requests;   /* requests per batch, 1..65536 */
+    uint64_t max_batch_bytes;      /* message bytes per batch (capped at the budget) */
+    uint64_t long_threshold_perms; /* requests costing more permutations go to the
+                                      long lane (0 = 64) */
+    uint32_t long_lane_kernel;     /* KB_SERVER_LONG_LANE_PARALLEL (0, default: one
+                                      warp per long request) or
+                                      KB_SERVER_LONG_THREAD_PER_REQUEST (1) */
+    uint32_t reserved;
+} kb_server_config;
+#define KB_SERVER_LONG_LANE_PARALLEL 0
+#define KB_SERVER_LONG_THREAD_PER_REQUEST 1
+
+typedef struct {
+    uint64_t requests;                /* completed by the replay */
+    uint64_t message_bytes;           /* their message bytes */
+    uint64_t batches;                 /* batches launched by the server so far */
+    uint64_t max_batch_requests_seen; /* largest batch so far */
+    uint64_t peak_arena_bytes;        /* peak arena bytes in use (the admitted load) */
+    uint64_t rejected;                /* requests refused as larger than the budget */
+    uint32_t completion_ring;         /* 1: per-request completion, 0: per batch */
+    uint32_t reserved;
+    double wall_s;                    /* first arrival to last completion */
+    double throughput_rps, throughput_gbs;
+    double lat_mean_us, lat_p50_us, lat_p90_us, lat_p99_us, lat_p999_us, lat_max_us;
+} kb_server_stats;
+
+/* Creates a server on the current device; NULL on error (*status says why:
+ * KB_ERR_INVALID for a bad config, KB_ERR_NOMEM, KB_ERR_CUDA). */
+kb_server *kb_server_create(const kb_server_config *cfg, int *status);
+/* Waits for outstanding requests (up to 60 s), stops the server, frees it. */
+void kb_server_destroy(kb_server *server);
+/* Queues one request and returns at once; *ticket (HOST, may be NULL)
+ * identifies it.  variant/out_len as in keccak_batch (out_len <= 1 MiB).
+ * KB_ERR_TOO_LARGE when the message can never fit the budget. */
+int kb_server_submit(kb_server *server, const uint8_t *msg, uint64_t len, int variant, uint32_t out_len,
+                     uint8_t *out, uint64_t *ticket);
+/* Waits until request `ticket` has completed: KB_OK, KB_ERR_TIMEOUT, or the
+ * server's error status. */
+int kb_server_wait(kb_server *server, uint64_t ticket, int timeout_ms);
+/* Waits until every submitted request has completed (timeout_ms < 0: no limit). */
+int kb_server_drain(kb_server *server, int timeout_ms);
+/*
+ * kb_server_replay -- drives the server with a recorded arrival schedule:
+ * request i (message pool + offsets[i], lens[i] bytes, variants[i],
+ * out_lens[i]) is submitted at arrival_ns[i] nanoseconds after the start
+ * (non-decreasing); outputs are packed in request order into `outputs`
+ * (HOST, device-visible, sum(out_lens) bytes).  Latency of a request = its
+ * completion time minus its scheduled arrival.  Fills latency_ns[i] (HOST,
+ * may be NULL) and *stats (HOST, may be NULL).  Synchronous; the caller must
+ * not submit to the same server meanwhile.
+ */
+int kb_server_replay(kb_server *server, const uint8_t *pool, const uint64_t *offsets, const uint64_t *lens,
+                     const uint8_t *variants, const uint32_t *out_lens, const int64_t *arrival_ns, uint64_t n,
+                     uint8_t *outputs, int64_t *latency_ns, kb_server_stats *stats);
+
 /* Synchronises `stream`, returns the device status word (KB_DEV_* bits, 0 if
  * clean) accumulated by kernels on this device since the last call, and
  * clears it.  Returns KB_ERR_CUDA if the synchronisation fails. */
@@ -214,8 +296,11 @@ void keccak_release(void);
 #define KB_REP_INTERLEAVED 1
 /*   KB_TUNE_RAGGED_SCHEDULE: how keccak_batch orders its work --
  *     KB_SCHEDULE_QUEUE (default: messages sorted into cost buckets, longest
- *     first, consumed by one persistent launch) or KB_SCHEDULE_INPUT_ORDER (one
- *     thread per message in input order, the plain one-launch control).
+ *     first, consumed by one persistent launch, one thread per message),
+ *     KB_SCHEDULE_LANE_PARALLEL (the same order, one warp per message: the 25
+ *     state lanes on 25 threads; about 2x lower latency per message at about
+ *     4x the instructions, for few long messages) or KB_SCHEDULE_INPUT_ORDER
+ *     (one thread per message in input order, the plain one-launch control).
  *   KB_TUNE_GRAPHS: 1 (default) replays the queue schedule's launches from a
  *     CUDA graph cached per call signature (pointers, n, stream); 0 launches
  *     directly.  Work issued on the legacy default stream or on a stream that
@@ -230,6 +315,7 @@ void keccak_release(void);
 #define KB_TUNE_RAGGED_SCHEDULE 1
 #define KB_SCHEDULE_INPUT_ORDER 0
 #define KB_SCHEDULE_QUEUE 1
+#define KB_SCHEDULE_LANE_PARALLEL 2
 #define KB_TUNE_GRAPHS 2
 #define KB_TUNE_AUTOTUNE 3
 #define KB_TUNE_QUEUE_MIN_BLOCKS 4

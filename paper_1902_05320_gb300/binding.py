@@ -180,7 +180,7 @@ KB_TUNE_REPRESENTATION = 0
 KB_REP_PLAIN, KB_REP_INTERLEAVED = 0, 1
 KB_TUNE_RAGGED_SCHEDULE, KB_TUNE_GRAPHS, KB_TUNE_AUTOTUNE = 1, 2, 3
 KB_TUNE_QUEUE_MIN_BLOCKS, KB_TUNE_QUEUE_BLOCKS_PER_SM = 4, 5
-KB_SCHEDULE_INPUT_ORDER, KB_SCHEDULE_QUEUE = 0, 1
+KB_SCHEDULE_INPUT_ORDER, KB_SCHEDULE_QUEUE, KB_SCHEDULE_LANE_PARALLEL = 0, 1, 2
 
 
 def keccak_tune_set(key: int, value: int) -> None:

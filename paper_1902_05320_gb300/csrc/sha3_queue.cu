@@ -24,6 +24,7 @@
 #include <tuple>
 
 #include "keccak_core.cuh"
+#include "lane_parallel.cuh"
 #include "runtime.cuh"
 #include "scan.cuh"
 #include "sponge.cuh"
@@ -161,6 +162,33 @@ __global__ void __launch_bounds__(kThreads, MINB)
     }
 }
 
+// Lane-parallel schedule: each warp takes one message at a time from the same
+// longest-first order and runs its sponge across 25 threads.
+__global__ void __launch_bounds__(kThreads)
+    k_sha3_lanes(const uint8_t *__restrict__ msgs, const uint64_t *__restrict__ offsets,
+                 const uint64_t *__restrict__ lens, const uint8_t *__restrict__ variants,
+                 const uint32_t *__restrict__ out_lens, const uint64_t *__restrict__ out_off,
+                 const uint32_t *__restrict__ order, uint8_t *__restrict__ digests, uint64_t n, Control *ctl,
+                 unsigned int *status) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long idx = 0;
+        if (lane == 0) idx = atomicAdd(&ctl->head, 1ull);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= n) break;
+        const uint32_t i = order[idx];
+        const int v = variants[i];
+        const uint32_t dlen = out_lens[i];
+        if (v > 5 || (v < 4 && dlen != uint32_t(variant_digest(v)))) {
+            if (lane == 0) atomicOr(status, v > 5 ? KB_DEV_BAD_VARIANT : KB_DEV_BAD_OUTLEN);
+            continue;
+        }
+        const uint8_t *p = msgs + offsets[i];
+        if ((reinterpret_cast<uintptr_t>(p) & 7) == 0) lane_sponge<true>(p, lens[i], v, digests + out_off[i], dlen);
+        else lane_sponge<false>(p, lens[i], v, digests + out_off[i], dlen);
+    }
+}
+
 // Register budgets the tuner can choose (minimum resident blocks of 128
 // threads per SM, which caps registers per thread at 65536 / (128 x MINB)).
 const int kMinBlocksChoices[] = {4, 5, 6, 8};
@@ -177,6 +205,7 @@ const void *queue_kernel(int minb) {
 struct QueueConfig {
     int minb = 4;           // register budget (template instance)
     int blocks_per_sm = 0;  // 0: as many as fit
+    bool lanes = false;     // one warp per message (lane-parallel sponge)
 };
 
 struct Buffers {
@@ -202,6 +231,8 @@ Buffers carve(uint8_t *scratch, uint64_t n, uint64_t ntiles) {
 }
 
 uint64_t queue_grid(const QueueConfig &cfg, uint64_t n, const DeviceInfo &dev) {
+    if (cfg.lanes)
+        return persistent_grid(reinterpret_cast<const void *>(&k_sha3_lanes), kThreads, 0, n * 32, dev);
     uint64_t grid = persistent_grid(queue_kernel(cfg.minb), kThreads, 0, (n + 31) / 32 * 32, dev);
     if (cfg.blocks_per_sm > 0) grid = std::min<uint64_t>(grid, uint64_t(cfg.blocks_per_sm) * dev.sm_count);
     return grid;
@@ -217,7 +248,7 @@ int issue(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, co
     k_plan<<<1, kScanThreads, 0, stream>>>(bf.tile_sums, ntiles, bf.ctl);
     k_scatter<<<unsigned(ntiles), kScanThreads, 0, stream>>>(lens, variants, out_lens, n, bf.tile_sums, bf.out_off,
                                                              bf.order, bf.ctl);
-    const void *fn = queue_kernel(cfg.minb);
+    const void *fn = cfg.lanes ? reinterpret_cast<const void *>(&k_sha3_lanes) : queue_kernel(cfg.minb);
     void *args[] = {&msgs, &offsets, &lens, &variants, &out_lens, const_cast<uint64_t **>(&bf.out_off),
                     const_cast<uint32_t **>(&bf.order), &digests, &n, const_cast<Control **>(&bf.ctl),
                     const_cast<unsigned int **>(&dev.d_status)};
@@ -285,6 +316,7 @@ QueueConfig choose_config(uint64_t n, const DeviceInfo &dev) {
     }
     if (regs > 0) cfg.minb = int(regs);
     if (bps > 0) cfg.blocks_per_sm = int(bps);
+    cfg.lanes = tuning_get(KB_TUNE_RAGGED_SCHEDULE) == KB_SCHEDULE_LANE_PARALLEL;
     return cfg;
 }
 
@@ -313,8 +345,8 @@ int launch_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const uint
                         cudaStreamIsCapturing(stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
     if (!graphs) return issue(msgs, offsets, lens, variants, out_lens, digests, n, bf, ntiles, cfg, grid, stream, dev);
 
-    GraphKey key{{msgs, offsets, lens, variants, out_lens, digests, scratch}, n, stream, cfg.minb,
-                 cfg.blocks_per_sm, dev.device};
+    GraphKey key{{msgs, offsets, lens, variants, out_lens, digests, scratch}, n, stream,
+                 cfg.lanes ? -cfg.minb : cfg.minb, cfg.blocks_per_sm, dev.device};
     {
         std::lock_guard<std::mutex> lk(g_graph_mu);
         for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {

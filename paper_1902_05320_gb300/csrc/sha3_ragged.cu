@@ -2,8 +2,10 @@
 // the six variants in one call (the batch mode of Section 4 with the paper's
 // equal-length restriction of Section 4.3 lifted).
 //
-// Two schedules, chosen by KB_TUNE_RAGGED_SCHEDULE:
-//  * the cost-bucketed persistent work queue of sha3_queue.cu (default);
+// Three schedules, chosen by KB_TUNE_RAGGED_SCHEDULE:
+//  * the cost-bucketed persistent work queue of sha3_queue.cu (default), with
+//    one thread per message or, in its lane-parallel form, one warp per
+//    message;
 //  * input order, kept as the plain one-launch control: digest offsets by an
 //    exclusive prefix sum of out_lens (three small kernels), then one thread
 //    per message in a grid-stride loop.
@@ -90,7 +92,7 @@ uint64_t digest_offsets_tiles(uint64_t n) { return (n + kScanTile - 1) / kScanTi
 int launch_ragged(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
                   const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
                   const DeviceInfo &dev) {
-    if (tuning_get(KB_TUNE_RAGGED_SCHEDULE) == KB_SCHEDULE_QUEUE)
+    if (tuning_get(KB_TUNE_RAGGED_SCHEDULE) != KB_SCHEDULE_INPUT_ORDER)
         return launch_ragged_queue(msgs, offsets, lens, variants, out_lens, digests, n, stream, dev);
     // Input order: one thread per message, grid-stride.
     const uint64_t ntiles = digest_offsets_tiles(n);

@@ -97,3 +97,41 @@ def ragged_batch(n: int, seed: int, max_len: int = 65536, min_len: int = 0,
 
 def merkle_buffer(n_leaves: int, leaf_bytes: int, seed: int) -> np.ndarray:
     return random_bytes(n_leaves * leaf_bytes, seed)
+
+
+@dataclass
+class ServingWorkload:
+    pool: np.ndarray        # uint8 message pool
+    offsets: np.ndarray     # uint64[n]: request i's message starts at pool[offsets[i]]
+    lens: np.ndarray        # uint64[n]
+    variants: np.ndarray    # uint8[n]
+    out_lens: np.ndarray    # uint32[n]
+    arrival_ns: np.ndarray  # int64[n], non-decreasing
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets.size)
+
+
+def serving_workload(rate_per_s: float, seconds: float, seed: int, min_len: int = 32, max_len: int = 1 << 20,
+                     pool_bytes: int = 1 << 30, variants=(0, 1, 2, 3, 4, 5), shake_out=(16, 512)) -> ServingWorkload:
+    """Poisson arrivals at rate_per_s for `seconds`; each request one message of
+    log-uniform length in [min_len, max_len] taken at a seeded offset of a
+    random pool, a uniform variant and (SHAKE) a uniform output length."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.poisson(rate_per_s * seconds))
+    gaps = rng.exponential(1e9 / rate_per_s, size=n)
+    arrival = np.floor(np.cumsum(gaps)).astype(np.int64)
+    lo, hi = np.log(min_len), np.log(max_len + 1)
+    lens = np.clip(np.floor(np.exp(rng.uniform(lo, hi, size=n))), min_len, max_len).astype(np.uint64)
+    offsets = (rng.integers(0, 2**63, size=n, dtype=np.uint64) % (np.uint64(pool_bytes) - lens + np.uint64(1)))
+    var = rng.choice(np.asarray(variants, dtype=np.uint8), size=n).astype(np.uint8)
+    out_lens = np.empty(n, dtype=np.uint32)
+    for v in range(6):
+        sel = var == v
+        if DIGEST_BYTES[v] is not None:
+            out_lens[sel] = DIGEST_BYTES[v]
+        else:
+            out_lens[sel] = rng.integers(shake_out[0], shake_out[1] + 1, size=int(sel.sum()))
+    pool = random_bytes(pool_bytes, seed + 7_000_003)
+    return ServingWorkload(pool, offsets.astype(np.uint64), lens, var, out_lens, arrival)

@@ -298,7 +298,7 @@ def restore_tuning(cuda_lib):
         cuda_lib.keccak_tune_set(k, v)
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [0, 1, 2])
 @pytest.mark.parametrize("graphs", [0, 1])
 def test_ragged_schedules_match_oracle(cuda_lib, oracle_mod, restore_tuning, schedule, graphs):
     cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_RAGGED_SCHEDULE, schedule)
@@ -349,3 +349,21 @@ def test_autotune_keeps_digests(cuda_lib, oracle_mod, restore_tuning):
     out.zero_()
     cuda_lib.keccak_batch(*d, out, b.n)  # now runs with the tuned configuration
     assert np.array_equal(host(out)[: b.total_out()], want)
+
+
+def test_lane_parallel_long_messages_every_variant(cuda_lib, oracle_mod, restore_tuning):
+    # One warp per message: multi-block messages, every padding position of the
+    # final block, SHAKE outputs across squeeze blocks, aligned and unaligned.
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_RAGGED_SCHEDULE, cuda_lib.KB_SCHEDULE_LANE_PARALLEL)
+    lens, variants = [], []
+    for v in range(6):
+        r = RATES[v]
+        for L in (0, 1, r - 1, r, r + 1, 5 * r + 3, 20_000):
+            lens.append(L)
+            variants.append(v)
+    rng = np.random.default_rng(77)
+    b = W.ragged_batch(len(lens), seed=78, lens=np.array(lens), gap=5)
+    b.variants = np.array(variants, dtype=np.uint8)
+    b.out_lens = np.array([DIG[v] or int(rng.choice([0, 1, 167, 168, 169, 500])) for v in b.variants],
+                          dtype=np.uint32)
+    assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
