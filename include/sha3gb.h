@@ -153,14 +153,15 @@ int keccak_batch_noalloc(const uint8_t *msgs, const uint64_t *offsets, const uin
 
 /*
  * keccak_batch_uniform_host -- keccak_batch_uniform on HOST buffers, the whole
- * job: host-to-device copy of the messages, hashing, device-to-host copy of
- * the digests, pipelined in chunks over internal streams so copies overlap
- * with hashing.  Synchronous: returns when h_digests holds every output.
- *   h_msgs     host, (n-1)*stride + len bytes; page-locked memory gives full
- *              copy bandwidth, pageable memory works but is slower
+ * job including the transfers: the messages are copied to the device, hashed
+ * and the digests copied back in chunks pipelined over internal streams
+ * (cached device staging buffers), so copies overlap the hashing.  With
+ * KB_TUNE_HOST_PATH = KB_HOST_PATH_ZERO_COPY and page-locked buffers the
+ * kernel instead works on the host memory in place.  Synchronous: returns when h_digests holds every output.
+ *   h_msgs     host, (n-1)*stride + len bytes
  *   h_digests  host, n*out_len bytes
  * Other arguments as keccak_batch_uniform.  `stream` orders the job after
- * earlier work on that stream.  Uses cached device staging buffers.
+ * earlier work on that stream.
  */
 int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t len, int variant,
                               uint32_t out_len, uint8_t *h_digests, uint64_t n, void *stream);
@@ -320,6 +321,15 @@ void keccak_release(void);
 #define KB_TUNE_AUTOTUNE 3
 #define KB_TUNE_QUEUE_MIN_BLOCKS 4
 #define KB_TUNE_QUEUE_BLOCKS_PER_SM 5
+/*   KB_TUNE_HOST_PATH: how keccak_batch_uniform_host moves data --
+ *     KB_HOST_PATH_AUTO (default; currently the staged copies, which measure
+ *     faster on GB300), KB_HOST_PATH_STAGED (copy in chunks through device
+ *     buffers), KB_HOST_PATH_ZERO_COPY (the kernel reads and writes the
+ *     page-locked host buffers in place; KB_ERR_INVALID for pageable ones). */
+#define KB_TUNE_HOST_PATH 6
+#define KB_HOST_PATH_AUTO 0
+#define KB_HOST_PATH_STAGED 1
+#define KB_HOST_PATH_ZERO_COPY 2
 int keccak_tune_set(int key, int64_t value);
 int64_t keccak_tune_get(int key);
 

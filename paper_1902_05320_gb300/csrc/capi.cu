@@ -27,6 +27,18 @@ bool sizes_fit(uint64_t stride, uint64_t len, uint32_t out_len, uint64_t n) {
     return true;
 }
 
+// Device address of a host buffer the GPU can access (page-locked memory),
+// or nullptr for pageable memory.
+const void *device_view(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged) return a.devicePointer;
+    return nullptr;
+}
+
 // ---- host-buffer pipeline ---------------------------------------------------
 constexpr int kStages = 3;
 
@@ -170,6 +182,20 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    // In place (KB_HOST_PATH_ZERO_COPY): the kernel reads the messages and
+    // writes the digests in page-locked host memory directly.  Measured slower
+    // than the staged copies on GB300, so it is not the default.
+    const int64_t path = tuning_get(KB_TUNE_HOST_PATH);
+    const void *d_in = len ? device_view(h_msgs) : h_msgs;
+    const void *d_out = out_len ? device_view(h_digests) : h_digests;
+    if (path == KB_HOST_PATH_ZERO_COPY && d_in && d_out) {
+        cudaStream_t user = static_cast<cudaStream_t>(stream);
+        int rc = launch_uniform(static_cast<const uint8_t *>(d_in), stride, len, variant, out_len,
+                                static_cast<uint8_t *>(const_cast<void *>(d_out)), n, user, *dev);
+        if (rc == KB_OK && cudaStreamSynchronize(user) != cudaSuccess) rc = KB_ERR_CUDA;
+        return rc;
+    }
+    if (path == KB_HOST_PATH_ZERO_COPY) return KB_ERR_INVALID;  // asked for, but the buffers are pageable
     // Chunks of about 32 MiB of input (at least one message each).
     const uint64_t target = uint64_t(32) << 20;
     uint64_t chunk = stride ? std::max<uint64_t>(1, target / stride) : n;

@@ -94,10 +94,12 @@ void release_device() {
 }
 
 namespace {
-constexpr int kTuneKeys = 6;
+constexpr int kTuneKeys = 7;
 // Defaults: plain layout, cost-bucketed queue, graphs on, tuned configs used,
-// register budget and blocks per SM from the tuner (or built-in defaults).
-std::atomic<int64_t> g_tuning[kTuneKeys] = {{KB_REP_PLAIN}, {KB_SCHEDULE_QUEUE}, {1}, {1}, {0}, {0}};
+// register budget and blocks per SM from the tuner (or built-in defaults),
+// host buffers staged through device memory.
+std::atomic<int64_t> g_tuning[kTuneKeys] = {{KB_REP_PLAIN}, {KB_SCHEDULE_QUEUE}, {1}, {1}, {0}, {0},
+                                            {KB_HOST_PATH_AUTO}};
 }  // namespace
 
 int64_t tuning_get(int key) { return (key >= 0 && key < kTuneKeys) ? g_tuning[key].load() : -1; }
@@ -120,6 +122,9 @@ int tuning_set(int key, int64_t value) {
             break;
         case KB_TUNE_QUEUE_BLOCKS_PER_SM:
             if (value < 0 || value > 32) return KB_ERR_INVALID;
+            break;
+        case KB_TUNE_HOST_PATH:
+            if (value < KB_HOST_PATH_AUTO || value > KB_HOST_PATH_ZERO_COPY) return KB_ERR_INVALID;
             break;
         default:
             return KB_ERR_INVALID;

@@ -186,9 +186,11 @@ def test_merkle_unaligned_buffer(cuda_lib, oracle_mod):
 
 
 # -- host-buffer pipeline ---------------------------------------------------------------------
-@pytest.mark.parametrize("pinned", [True, False])
-def test_host_pipeline_matches_oracle(cuda_lib, oracle_mod, pinned):
+@pytest.mark.parametrize("pinned,path", [(True, 0), (True, 1), (False, 0), (False, 1)])
+def test_host_pipeline_matches_oracle(cuda_lib, oracle_mod, pinned, path):
     torch = _torch()
+    saved = cuda_lib.keccak_tune_get(cuda_lib.KB_TUNE_HOST_PATH)
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_HOST_PATH, path)
     n, L = 700_000, 64  # 44.8 MB of input: more than one 32 MiB chunk
     msgs = W.uniform_messages(n, L, seed=51)
     if pinned:
@@ -196,7 +198,10 @@ def test_host_pipeline_matches_oracle(cuda_lib, oracle_mod, pinned):
         h_out = torch.zeros(n * 32, dtype=torch.uint8).pin_memory()
     else:
         h_in, h_out = msgs, np.zeros(n * 32, dtype=np.uint8)
-    cuda_lib.keccak_batch_uniform_host(h_in, L, L, 1, 32, h_out, n)
+    try:
+        cuda_lib.keccak_batch_uniform_host(h_in, L, L, 1, 32, h_out, n)
+    finally:
+        cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_HOST_PATH, saved)
     got = (h_out.numpy() if pinned else h_out).reshape(n, 32)
     chunk = (32 << 20) // L
     idx = np.unique(np.concatenate([np.arange(5), np.arange(chunk - 3, chunk + 3), np.arange(n - 5, n),
@@ -291,7 +296,7 @@ def test_interleaved_control_matches_oracle(cuda_lib, oracle_mod):
 # -- ragged schedules, graph replay, autotuner -------------------------------------------
 @pytest.fixture
 def restore_tuning(cuda_lib):
-    keys = range(6)
+    keys = range(7)
     saved = [cuda_lib.keccak_tune_get(k) for k in keys]
     yield
     for k, v in zip(keys, saved):
