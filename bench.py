@@ -71,6 +71,30 @@ def ops_per_permutation() -> int:
 
 
 # ---------------------------------------------------------------------------
+# Replicas: every rank hashes its own messages (seeded by rank), the step time
+# is the slowest rank's, and the value counts the messages of all ranks.
+def rank_seed(base: int, rank: int) -> int:
+    return base + rank
+
+
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's time (a collective on timing only, never on data)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mhash_s(n_per_rank: int, world: int, ms: float) -> float:
+    return world * n_per_rank / (ms / 1e3) / 1e6
+
+
+# ---------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -245,7 +269,7 @@ def main() -> None:
         return
 
     n_msgs = args.messages
-    msgs_np = workloads.uniform_messages(n_msgs, MSG_BYTES, seed=1 + rank)
+    msgs_np = workloads.uniform_messages(n_msgs, MSG_BYTES, seed=rank_seed(1, rank))
     msgs = torch.from_numpy(msgs_np).cuda()
     digests = torch.empty(n_msgs * DIGEST, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -282,13 +306,10 @@ def main() -> None:
     ms = start.elapsed_time(end) / args.steps
     time.sleep(0.2)
     sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     clocks = sampler.summary()
 
-    value = world * n_msgs / (ms / 1e3) / 1e6
+    value = whole_job_mhash_s(n_msgs, world, ms)
     ops_perm = ops_per_permutation()
     achieved = n_msgs * ops_perm / (ms / 1e3) / 1e12
     peak = SM_COUNT_GB300 * INT_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12

@@ -9,7 +9,8 @@
 // Kernels: one thread per leaf (the prefixed message is read through a
 // one-byte funnel shift of the leaf's aligned words), then one launch per
 // level with one thread per parent node (0x01 || left || right is exactly one
-// 65-byte block at rate 136).
+// 65-byte block at rate 136) while a level has more than 4096 nodes, and one
+// single-block launch for all the levels above.
 #include <cuda_runtime.h>
 
 #include "keccak_core.cuh"
@@ -125,40 +126,64 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     }
 }
 
-// One level: parent j = SHA3-256(0x01 || in[2j] || in[2j+1]); for an odd
+// Parent j of one level: SHA3-256(0x01 || in[2j] || in[2j+1]); for an odd
 // count the last child is copied to out[count/2].  `in` is 32-byte aligned.
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
-    k_merkle_level(const uint8_t *__restrict__ in, uint64_t count, uint8_t *__restrict__ out) {
+// No __restrict__: in the top-of-tree kernel a level written by the block is
+// read back by it after a barrier, so the loads must stay coherent ones.
+__device__ __forceinline__ void merkle_parent(const uint8_t *in, uint64_t count, uint8_t *out, uint64_t j) {
     const uint64_t pairs = count / 2;
+    if (j == pairs) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(in + 32 * (count - 1));
+        uint4 *d = reinterpret_cast<uint4 *>(out + 32 * j);
+        d[0] = s[0];
+        d[1] = s[1];
+        return;
+    }
+    uint32_t A[25], B[25];
+#pragma unroll
+    for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
+    const uint4 *q = reinterpret_cast<const uint4 *>(in + 64 * j);
+    uint32_t carry = 0x01u << 24;  // node prefix byte
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const uint4 v = q[t];
+        uint32_t vlo, vhi;
+        prefixed_word(carry, v.x, v.y, vlo, vhi);
+        PlainRep::set_word(A[2 * t], B[2 * t], vlo, vhi);
+        prefixed_word(carry, v.z, v.w, vlo, vhi);
+        PlainRep::set_word(A[2 * t + 1], B[2 * t + 1], vlo, vhi);
+    }
+    // Word 8: the last child byte, then the domain byte at message offset 65.
+    uint32_t vlo = (carry >> 24) | (uint32_t(kDomain) << 8), vhi = 0;
+    PlainRep::set_word(A[8], B[8], vlo, vhi);
+    B[kRate / 8 - 1] ^= 0x80000000u;
+    PlainRep::permute<true>(A, B);
+    squeeze<kRate, PlainRep>(A, B, out + 32 * j, 32);
+}
+
+// One level, one thread per parent.
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_merkle_level(const uint8_t *in, uint64_t count, uint8_t *out) {
+    const uint64_t parents = count / 2 + (count & 1);
     const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < pairs + (count & 1); j += step) {
-        if (j == pairs) {
-            const uint4 *s = reinterpret_cast<const uint4 *>(in + 32 * (count - 1));
-            uint4 *d = reinterpret_cast<uint4 *>(out + 32 * j);
-            d[0] = s[0];
-            d[1] = s[1];
-            continue;
-        }
-        uint32_t A[25], B[25];
-#pragma unroll
-        for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
-        const uint4 *q = reinterpret_cast<const uint4 *>(in + 64 * j);
-        uint32_t carry = 0x01u << 24;  // node prefix byte
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const uint4 v = __ldg(q + t);
-            uint32_t vlo, vhi;
-            prefixed_word(carry, v.x, v.y, vlo, vhi);
-            PlainRep::set_word(A[2 * t], B[2 * t], vlo, vhi);
-            prefixed_word(carry, v.z, v.w, vlo, vhi);
-            PlainRep::set_word(A[2 * t + 1], B[2 * t + 1], vlo, vhi);
-        }
-        // Word 8: the last child byte, then the domain byte at message offset 65.
-        uint32_t vlo = (carry >> 24) | (uint32_t(kDomain) << 8), vhi = 0;
-        PlainRep::set_word(A[8], B[8], vlo, vhi);
-        B[kRate / 8 - 1] ^= 0x80000000u;
-        PlainRep::permute<true>(A, B);
-        squeeze<kRate, PlainRep>(A, B, out + 32 * j, 32);
+    for (uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < parents; j += step)
+        merkle_parent(in, count, out, j);
+}
+
+// The top of the tree, from a level of at most kTopCount nodes up to the
+// root, in one block: a block barrier separates the levels (each level is
+// written to global memory, which the barrier makes visible to the block).
+constexpr int kTopThreads = 512;
+constexpr uint64_t kTopCount = 4096;
+
+__global__ void __launch_bounds__(kTopThreads) k_merkle_top(uint8_t *level, uint64_t count) {
+    while (count > 1) {
+        uint8_t *next = level + 32 * count;
+        const uint64_t parents = count / 2 + (count & 1);
+        for (uint64_t j = threadIdx.x; j < parents; j += kTopThreads) merkle_parent(level, count, next, j);
+        __syncthreads();
+        level = next;
+        count = parents;
     }
 }
 
@@ -186,7 +211,7 @@ int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_by
     if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
     uint8_t *level = nodes;
     uint64_t n = n_leaves;
-    while (n > 1) {
+    while (n > kTopCount) {
         uint8_t *next = level + 32 * n;
         const uint64_t parents = n / 2 + (n & 1);
         grid = persistent_grid(reinterpret_cast<const void *>(&k_merkle_level), kThreads, 0, parents, dev);
@@ -194,6 +219,10 @@ int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_by
         if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
         level = next;
         n = parents;
+    }
+    if (n > 1) {
+        k_merkle_top<<<1, kTopThreads, 0, stream>>>(level, n);
+        if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
     }
     return KB_OK;
 }
