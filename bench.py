@@ -238,6 +238,8 @@ def main() -> None:
                     help="messages per step (default 2^24; smaller only for profiling captures)")
     ap.add_argument("--serving-only", type=float, default=0.0, metavar="SECONDS",
                     help="only run the serving measurement for SECONDS of arrivals")
+    ap.add_argument("--merkle-only", type=int, default=0, metavar="LEAVES",
+                    help="only run the Merkle measurement on LEAVES 8 KiB leaves (profiling captures)")
     ap.add_argument("--ragged-only", type=int, default=0, metavar="N",
                     help="only run the ragged-batch measurement on N messages (profiling captures)")
     args = ap.parse_args()
@@ -262,6 +264,10 @@ def main() -> None:
     binding.load()
     if args.serving_only:
         print(json.dumps(serving_measurements(workloads, torch, rank, seconds=args.serving_only)), flush=True)
+        return
+    if args.merkle_only:
+        print(json.dumps(merkle_measurements(binding, workloads, torch, torch.cuda.current_stream(), rank,
+                                             n_leaves=args.merkle_only)), flush=True)
         return
     if args.ragged_only:
         print(json.dumps(ragged_measurements(binding, workloads, torch, torch.cuda.current_stream(), rank,

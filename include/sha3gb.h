@@ -167,6 +167,30 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
                               uint32_t out_len, uint8_t *h_digests, uint64_t n, void *stream);
 
 /*
+ * Streaming (incremental) hashing of n messages at once, for messages that
+ * arrive in pieces or are larger than one call should hold: the sponge of
+ * Section 3.2 paused between calls.  Each message has a state of
+ * KB_STATE_BYTES bytes in device memory (the caller allocates n of them, back
+ * to back, 8-byte aligned): its 25 lanes and the bytes of the block not yet
+ * complete.  Pieces may have any length; the digest equals the one-shot hash
+ * of the concatenated pieces.
+ *   keccak_stream_init: states for variants[i] (device uint8[n]).
+ *   keccak_stream_absorb: appends piece i (msgs + offsets[i], lens[i] bytes;
+ *     lens[i] = 0 is allowed) to message i.
+ *   keccak_stream_final: pads and squeezes out_lens[i] bytes (digest size for
+ *     SHA3-x) into digests at the exclusive scan of out_lens, as
+ *     keccak_batch does; a finalised state refuses further pieces.
+ * Errors per message (unknown variant, wrong SHA3 output size, absorbing into
+ * or finalising a finalised state) set KB_DEV_* bits and skip that message.
+ * Stream-ordered; calls on the same states must be ordered by the caller.
+ */
+#define KB_STATE_BYTES 384
+int keccak_stream_init(uint8_t *states, const uint8_t *variant, uint64_t n, void *stream);
+int keccak_stream_absorb(uint8_t *states, const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                         uint64_t n, void *stream);
+int keccak_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *digests, uint64_t n, void *stream);
+
+/*
  * merkle_sha3_256 -- tree mode (Section 4: messages "hashed in twos until the
  * Hash Root").  The buffer holds n_leaves leaves of leaf_bytes bytes each;
  * leaf digest = SHA3-256(0x00 || leaf), node digest = SHA3-256(0x01 || left

@@ -55,6 +55,9 @@ _SIGS = {
     "keccak_batch_uniform_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                                  ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
                                                  ctypes.c_void_p]),
+    "keccak_stream_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "keccak_stream_absorb": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_uint64, ctypes.c_void_p]),
+    "keccak_stream_final": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_uint64, ctypes.c_void_p]),
     "merkle_sha3_256": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
                                        ctypes.c_void_p]),
     "merkle_node_count": (ctypes.c_uint64, [ctypes.c_uint64]),
@@ -150,6 +153,23 @@ def keccak_batch_uniform_host(h_msgs, stride: int, length: int, variant: int, ou
                               n: int, stream=None) -> None:
     _check(load().keccak_batch_uniform_host(_ptr(h_msgs), stride, length, variant, out_len, _ptr(h_digests),
                                             n, _stream(stream)), "keccak_batch_uniform_host")
+
+
+KB_STATE_BYTES = 384
+
+
+def keccak_stream_init(states, variants, n: int, stream=None) -> None:
+    _check(load().keccak_stream_init(_ptr(states), _ptr(variants), n, _stream(stream)), "keccak_stream_init")
+
+
+def keccak_stream_absorb(states, msgs, offsets, lens, n: int, stream=None) -> None:
+    _check(load().keccak_stream_absorb(_ptr(states), _ptr(msgs), _ptr(offsets), _ptr(lens), n, _stream(stream)),
+           "keccak_stream_absorb")
+
+
+def keccak_stream_final(states, out_lens, digests, n: int, stream=None) -> None:
+    _check(load().keccak_stream_final(_ptr(states), _ptr(out_lens), _ptr(digests), n, _stream(stream)),
+           "keccak_stream_final")
 
 
 def merkle_sha3_256(buf, n_leaves: int, leaf_bytes: int, stream=None) -> bytes:

@@ -229,6 +229,37 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
     return rc;
 }
 
+int keccak_stream_init(uint8_t *states, const uint8_t *variant, uint64_t n, void *stream) {
+    if (n == 0) return KB_OK;
+    if (!states || !variant || n > UINT64_MAX / KB_STATE_BYTES) return KB_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(states) & 7) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    return launch_stream_init(states, variant, n, static_cast<cudaStream_t>(stream), *dev);
+}
+
+int keccak_stream_absorb(uint8_t *states, const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                         uint64_t n, void *stream) {
+    if (n == 0) return KB_OK;
+    if (!states || !msgs || !offsets || !lens || n > UINT64_MAX / KB_STATE_BYTES) return KB_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(states) & 7) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    return launch_stream_absorb(states, msgs, offsets, lens, n, static_cast<cudaStream_t>(stream), *dev);
+}
+
+int keccak_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *digests, uint64_t n, void *stream) {
+    if (n == 0) return KB_OK;
+    if (!states || !out_lens || !digests || n > UINT32_MAX) return KB_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(states) & 7) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    return launch_stream_final(states, out_lens, digests, n, static_cast<cudaStream_t>(stream), *dev);
+}
+
 int keccak_last_error(void *stream) {
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);

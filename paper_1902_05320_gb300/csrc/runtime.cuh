@@ -61,6 +61,15 @@ int launch_ragged_external(const uint8_t *msgs, const uint64_t *offsets, const u
                            uint64_t *out_off, uint64_t *tile_sums, unsigned int *status, int sm_count,
                            cudaStream_t stream);
 uint64_t digest_offsets_tiles(uint64_t n);
+int launch_digest_offsets(const uint32_t *out_lens, uint64_t n, uint64_t *out_off, uint64_t *tile_sums,
+                          cudaStream_t stream);
+// Streaming states (stream.cu).
+int launch_stream_init(uint8_t *states, const uint8_t *variants, uint64_t n, cudaStream_t stream,
+                       const DeviceInfo &dev);
+int launch_stream_absorb(uint8_t *states, const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                         uint64_t n, cudaStream_t stream, const DeviceInfo &dev);
+int launch_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
+                        cudaStream_t stream, const DeviceInfo &dev);
 // Cost-bucketed persistent path (sha3_queue.cu).
 int launch_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
                         const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
