@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
             L.oracle_merkle_levels.restype = ctypes.c_int
             L.oracle_merkle_sha3_256.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, u8p]
             L.oracle_merkle_sha3_256.restype = ctypes.c_int
+            L.oracle_merkle_message.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, u8p]
+            L.oracle_merkle_message.restype = ctypes.c_int
             L.oracle_hash_batch.argtypes = [u8p, u64p, u64p, u8p, u32p, u8p, ctypes.c_uint64,
                                             ctypes.c_int]
             L.oracle_hash_batch.restype = ctypes.c_int
@@ -216,6 +218,16 @@ def merkle_root(buf, n_leaves: int, leaf_bytes: int) -> bytes:
     root = np.zeros(32, dtype=np.uint8)
     if lib().oracle_merkle_sha3_256(_p(b), n_leaves, leaf_bytes, _p(root)) != OK:
         raise ValueError("invalid tree")
+    return root.tobytes()
+
+
+def merkle_message_root(msg, chunk_bytes: int) -> bytes:
+    """Root of the tree over one message cut into chunk_bytes chunks."""
+    m = _bytes_arr(msg)
+    root = np.zeros(32, dtype=np.uint8)
+    src = m if m.size else np.zeros(1, np.uint8)
+    if lib().oracle_merkle_message(_p(src), m.size, chunk_bytes, _p(root)) != OK:
+        raise ValueError("invalid chunk size")
     return root.tobytes()
 
 

@@ -390,3 +390,38 @@ int oracle_merkle_sha3_256(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_
     free(nodes);
     return rc;
 }
+
+/* The same tree over one message cut into chunks of chunk_bytes bytes (the
+ * last chunk shorter, an empty message giving one empty leaf): the tree mode
+ * applied to a single large input, which Section 1 names as the way to spread
+ * one long message over parallel hardware.  Leaf and node rules as above. */
+int oracle_merkle_message(const uint8_t *msg, uint64_t len, uint64_t chunk_bytes, uint8_t root[32]) {
+    if (chunk_bytes == 0 || (len > 0 && !msg) || !root) return ORACLE_ERR_INVALID;
+    uint64_t n = len == 0 ? 1 : (len + chunk_bytes - 1) / chunk_bytes;
+    uint8_t *level = (uint8_t *)malloc(32 * n);
+    uint8_t *tmp = (uint8_t *)malloc(1 + (chunk_bytes > 64 ? chunk_bytes : 64));
+    if (!level || !tmp) { free(level); free(tmp); return ORACLE_ERR_NOMEM; }
+    int rc = ORACLE_OK;
+    tmp[0] = 0x00;
+    for (uint64_t i = 0; i < n && rc == ORACLE_OK; ++i) {
+        uint64_t start = i * chunk_bytes;
+        uint64_t take = len - start < chunk_bytes ? len - start : chunk_bytes;
+        if (len == 0) take = 0;
+        if (take) memcpy(tmp + 1, msg + start, take);
+        rc = oracle_hash(1, tmp, 1 + take, level + 32 * i, 32);
+    }
+    tmp[0] = 0x01;
+    while (n > 1 && rc == ORACLE_OK) {
+        uint64_t pairs = n / 2;
+        for (uint64_t j = 0; j < pairs && rc == ORACLE_OK; ++j) {
+            memcpy(tmp + 1, level + 64 * j, 64);
+            rc = oracle_hash(1, tmp, 65, level + 32 * j, 32);
+        }
+        if (n & 1) memmove(level + 32 * pairs, level + 32 * (n - 1), 32);
+        n = pairs + (n & 1);
+    }
+    if (rc == ORACLE_OK) memcpy(root, level, 32);
+    free(level);
+    free(tmp);
+    return rc;
+}

@@ -61,6 +61,8 @@ int oracle_inc_final(oracle_inc *st, uint8_t *out, size_t out_len);
 uint64_t oracle_merkle_node_count(uint64_t n_leaves);
 int oracle_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes);
 int oracle_merkle_sha3_256(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t root[32]);
+/* The tree of one message cut into chunk_bytes chunks (last one shorter). */
+int oracle_merkle_message(const uint8_t *msg, uint64_t len, uint64_t chunk_bytes, uint8_t root[32]);
 
 /* Batch harness (batch.c): hashes n messages on nthreads host threads.
  * Message i is msgs[offsets[i] .. offsets[i]+lens[i]), its variant

@@ -65,3 +65,13 @@ def test_merkle_rejects_empty(oracle_mod):
         oracle_mod.merkle_root(b"", 0, 8)
     with pytest.raises(ValueError):
         oracle_mod.merkle_root(b"abc", 1, 0)
+
+
+@pytest.mark.parametrize("length,chunk", [(0, 64), (1, 64), (64, 64), (65, 64), (1000, 64), (1000, 999),
+                                          (4097, 128), (777, 1), (3000, 136), (135, 136)])
+def test_message_tree_matches_recursive_definition(oracle_mod, length, chunk):
+    # One message cut into chunks (last one shorter; empty message = one empty
+    # leaf), the same leaf/node rules, against the recursive definition.
+    msg = np.random.default_rng(length + chunk).integers(0, 256, size=length, dtype=np.uint8).tobytes()
+    leaves = [msg[i:i + chunk] for i in range(0, length, chunk)] or [b""]
+    assert oracle_mod.merkle_message_root(msg, chunk) == _recursive_root(leaves)
