@@ -204,6 +204,34 @@ int keccak_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *dige
 int merkle_sha3_256(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *root,
                     void *stream);
 
+/*
+ * merkle_sha3_256_many -- many small trees at once, one thread per tree: the
+ * "one thread one tree" granularity Section 4.1 names for tree mode.  Tree t
+ * is leaves t*leaves_per_tree .. (t+1)*leaves_per_tree - 1 of buf (leaf_bytes
+ * bytes each), with the leaf/node rules of merkle_sha3_256; its root goes to
+ * roots + 32*t.
+ *   buf    device, n_trees*leaves_per_tree*leaf_bytes bytes, any alignment
+ *   roots  device, 32*n_trees bytes, 16-byte aligned
+ * Stream-ordered.  n_trees == 0 is a no-op; leaves_per_tree == 0 or >= 2^39,
+ * or leaf_bytes == 0, is KB_ERR_INVALID.  Each thread works through its tree
+ * sequentially, so this suits many trees of modest size; one large tree is
+ * faster with merkle_sha3_256.
+ */
+int merkle_sha3_256_many(const uint8_t *buf, uint64_t n_trees, uint64_t leaves_per_tree, uint64_t leaf_bytes,
+                         uint8_t *roots, void *stream);
+
+/*
+ * merkle_sha3_256_message -- the same tree over ONE message cut into chunks
+ * of chunk_bytes bytes (the last chunk shorter; an empty message is one empty
+ * leaf): tree hashing of a single large input, the way the paper's Section 1
+ * names for spreading one long message over parallel hardware.  The root is
+ * a different value from SHA3-256(msg): a digest of its own kind.
+ *   msg    device, len bytes (may be NULL when len == 0), any alignment
+ *   root   HOST, 32 bytes, written before the call returns
+ * Synchronous on `stream`.  chunk_bytes == 0 is KB_ERR_INVALID.
+ */
+int merkle_sha3_256_message(const uint8_t *msg, uint64_t len, uint64_t chunk_bytes, uint8_t *root, void *stream);
+
 /* Number of nodes in the tree of n_leaves leaves, all levels counted (0 for 0). */
 uint64_t merkle_node_count(uint64_t n_leaves);
 

@@ -60,6 +60,10 @@ _SIGS = {
     "keccak_stream_final": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_uint64, ctypes.c_void_p]),
     "merkle_sha3_256": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
                                        ctypes.c_void_p]),
+    "merkle_sha3_256_many": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "merkle_sha3_256_message": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
     "merkle_node_count": (ctypes.c_uint64, [ctypes.c_uint64]),
     "merkle_sha3_256_levels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
                                               ctypes.c_void_p]),
@@ -176,6 +180,18 @@ def merkle_sha3_256(buf, n_leaves: int, leaf_bytes: int, stream=None) -> bytes:
     root = (ctypes.c_uint8 * 32)()
     _check(load().merkle_sha3_256(_ptr(buf), n_leaves, leaf_bytes, ctypes.addressof(root), _stream(stream)),
            "merkle_sha3_256")
+    return bytes(root)
+
+
+def merkle_sha3_256_many(buf, n_trees: int, leaves_per_tree: int, leaf_bytes: int, roots, stream=None) -> None:
+    _check(load().merkle_sha3_256_many(_ptr(buf), n_trees, leaves_per_tree, leaf_bytes, _ptr(roots),
+                                       _stream(stream)), "merkle_sha3_256_many")
+
+
+def merkle_sha3_256_message(msg, length: int, chunk_bytes: int, stream=None) -> bytes:
+    root = (ctypes.c_uint8 * 32)()
+    _check(load().merkle_sha3_256_message(_ptr(msg), length, chunk_bytes, ctypes.addressof(root), _stream(stream)),
+           "merkle_sha3_256_message")
     return bytes(root)
 
 

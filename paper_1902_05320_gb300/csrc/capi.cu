@@ -173,6 +173,39 @@ int merkle_sha3_256(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, 
     return KB_OK;
 }
 
+int merkle_sha3_256_many(const uint8_t *buf, uint64_t n_trees, uint64_t leaves_per_tree, uint64_t leaf_bytes,
+                         uint8_t *roots, void *stream) {
+    if (n_trees == 0) return KB_OK;
+    if (!buf || !roots || leaves_per_tree == 0 || leaf_bytes == 0) return KB_ERR_INVALID;
+    if (leaves_per_tree >= (uint64_t(1) << 39)) return KB_ERR_INVALID;
+    if (leaves_per_tree > UINT64_MAX / leaf_bytes || n_trees > UINT64_MAX / (leaves_per_tree * leaf_bytes))
+        return KB_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(roots) & 15) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    return launch_merkle_many(buf, n_trees, leaves_per_tree, leaf_bytes, roots, static_cast<cudaStream_t>(stream),
+                              *dev);
+}
+
+int merkle_sha3_256_message(const uint8_t *msg, uint64_t len, uint64_t chunk_bytes, uint8_t *root, void *stream) {
+    if (chunk_bytes == 0 || !root || (len > 0 && !msg)) return KB_ERR_INVALID;
+    const uint64_t n = merkle_message_leaves(len, chunk_bytes);
+    if (n > (UINT64_MAX >> 7)) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t total = merkle_nodes(n);
+    uint8_t *nodes = static_cast<uint8_t *>(stream_scratch(s, size_t(32 * total), &err));
+    if (!nodes) return err;
+    if ((err = launch_merkle_message(msg, len, chunk_bytes, nodes, s, *dev)) != KB_OK) return err;
+    if (cudaMemcpyAsync(root, nodes + 32 * (total - 1), 32, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return KB_ERR_CUDA;
+    return KB_OK;
+}
+
 int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t len, int variant,
                               uint32_t out_len, uint8_t *h_digests, uint64_t n, void *stream) {
     if (variant < 0 || variant > 5 || !valid_out_len(variant, out_len)) return KB_ERR_INVALID;

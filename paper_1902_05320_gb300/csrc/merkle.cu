@@ -187,6 +187,123 @@ __global__ void __launch_bounds__(kTopThreads) k_merkle_top(uint8_t *level, uint
     }
 }
 
+// ---- many small trees, one thread per tree ----------------------------------
+
+// SHA3-256(0x00 || leaf) of leaf_bytes bytes at p (any alignment), as the
+// eight little-endian 32-bit words of the digest.
+__device__ __forceinline__ void leaf_digest(const uint8_t *p, uint64_t leaf_bytes, uint32_t (&d)[8]) {
+    const uint64_t vlen = leaf_bytes + 1;
+    const uint64_t nfull = vlen / kRate;
+    const uint32_t rem = uint32_t(vlen - nfull * kRate);
+    uint32_t A[25], B[25];
+#pragma unroll
+    for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
+    for (uint64_t b = 0; b <= nfull; ++b) {
+        const uint32_t valid = b < nfull ? uint32_t(kRate) : rem;
+#pragma unroll
+        for (int k = 0; k < kRate / 8; ++k) {
+            const uint64_t v0 = b * kRate + 8 * k;  // virtual bytes [v0, v0+8) = leaf bytes [v0-1, v0+7)
+            uint32_t lo = 0, hi = 0;
+            if (uint32_t(8 * k) < valid) {
+                const uint32_t nv = valid - 8 * k < 8 ? valid - 8 * k : 8;
+                if (v0 == 0) {
+                    if (nv > 1) ld_word_any(p, nv - 1, lo, hi);
+                    hi = __funnelshift_l(lo, hi, 8);
+                    lo = lo << 8;  // prefix byte 0x00
+                } else {
+                    ld_word_any(p + (v0 - 1), nv, lo, hi);
+                }
+            }
+            if (b == nfull) {
+                if (uint32_t(k) == rem / 8) {
+                    const uint32_t sh = (rem % 8) * 8;
+                    if (sh < 32) lo ^= uint32_t(kDomain) << sh;
+                    else hi ^= uint32_t(kDomain) << (sh - 32);
+                }
+                if (k == kRate / 8 - 1) hi ^= 0x80000000u;
+            }
+            PlainRep::xor_word(A[k], B[k], lo, hi);
+        }
+        PlainRep::permute<false>(A, B);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        d[2 * k] = A[k];
+        d[2 * k + 1] = B[k];
+    }
+}
+
+// SHA3-256(0x01 || left || right) from digests held as words.
+__device__ __forceinline__ void node_digest(const uint32_t (&l)[8], const uint32_t (&r)[8], uint32_t (&d)[8]) {
+    uint32_t A[25], B[25];
+#pragma unroll
+    for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
+    uint32_t carry = 0x01u << 24;  // node prefix byte
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const uint32_t lo = t < 4 ? l[2 * t] : r[2 * (t - 4)];
+        const uint32_t hi = t < 4 ? l[2 * t + 1] : r[2 * (t - 4) + 1];
+        uint32_t vlo, vhi;
+        prefixed_word(carry, lo, hi, vlo, vhi);
+        PlainRep::set_word(A[t], B[t], vlo, vhi);
+    }
+    PlainRep::set_word(A[8], B[8], (carry >> 24) | (uint32_t(kDomain) << 8), 0u);
+    B[kRate / 8 - 1] ^= 0x80000000u;
+    PlainRep::permute<true>(A, B);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        d[2 * k] = A[k];
+        d[2 * k + 1] = B[k];
+    }
+}
+
+// Stack of subtree digests: sizes are distinct powers of two (the binary
+// digits of the leaves seen so far), so 40 entries cover trees below 2^39.
+constexpr int kStackDepth = 40;
+
+// Tree t = leaves [t*L, (t+1)*L) of leaf_bytes each.  Leaves are hashed in
+// order; equal-size subtrees on the stack merge at once, and the remaining
+// ones merge right to left at the end, which builds exactly the level-by-
+// level tree with odd nodes carried up.
+__global__ void __launch_bounds__(kThreads)
+    k_merkle_many(const uint8_t *__restrict__ buf, uint64_t n_trees, uint64_t leaves_per_tree, uint64_t leaf_bytes,
+                  uint8_t *__restrict__ roots) {
+    const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n_trees; t += step) {
+        uint32_t stack[kStackDepth][8];
+        uint64_t size[kStackDepth];
+        int top = 0;
+        for (uint64_t i = 0; i < leaves_per_tree; ++i) {
+            uint32_t d[8];
+            leaf_digest(buf + (t * leaves_per_tree + i) * leaf_bytes, leaf_bytes, d);
+            uint64_t sz = 1;
+            while (top > 0 && size[top - 1] == sz) {
+                uint32_t l[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) l[k] = stack[top - 1][k];
+                node_digest(l, d, d);
+                sz *= 2;
+                --top;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) stack[top][k] = d[k];
+            size[top++] = sz;
+        }
+        uint32_t acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = stack[top - 1][k];
+        for (int j = top - 2; j >= 0; --j) {
+            uint32_t l[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) l[k] = stack[j][k];
+            node_digest(l, acc, acc);
+        }
+        uint4 *o = reinterpret_cast<uint4 *>(roots + 32 * t);
+        o[0] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+        o[1] = make_uint4(acc[4], acc[5], acc[6], acc[7]);
+    }
+}
+
 }  // namespace
 
 uint64_t merkle_nodes(uint64_t n_leaves) {
@@ -200,21 +317,28 @@ uint64_t merkle_nodes(uint64_t n_leaves) {
     return total;
 }
 
-int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes,
-                         cudaStream_t stream, const DeviceInfo &dev) {
-    const bool a8 = ((reinterpret_cast<uintptr_t>(buf) | leaf_bytes) & 7) == 0;
+namespace {
+
+int launch_leaves(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *out, cudaStream_t stream,
+                  const DeviceInfo &dev) {
+    if (n_leaves == 0) return KB_OK;
+    const bool a8 = ((reinterpret_cast<uintptr_t>(buf) | leaf_bytes) & 7) == 0 && leaf_bytes > 0;
     const void *fn = a8 ? reinterpret_cast<const void *>(&k_merkle_leaves_a8)
                         : reinterpret_cast<const void *>(&k_merkle_leaves_any);
-    uint64_t grid = persistent_grid(fn, kThreads, 0, n_leaves, dev);
-    if (a8) k_merkle_leaves_a8<<<unsigned(grid), kThreads, 0, stream>>>(buf, n_leaves, leaf_bytes, nodes);
-    else k_merkle_leaves_any<<<unsigned(grid), kThreads, 0, stream>>>(buf, n_leaves, leaf_bytes, nodes);
-    if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
+    const uint64_t grid = persistent_grid(fn, kThreads, 0, n_leaves, dev);
+    if (a8) k_merkle_leaves_a8<<<unsigned(grid), kThreads, 0, stream>>>(buf, n_leaves, leaf_bytes, out);
+    else k_merkle_leaves_any<<<unsigned(grid), kThreads, 0, stream>>>(buf, n_leaves, leaf_bytes, out);
+    return cuda_status(cudaGetLastError());
+}
+
+// Every level above the n leaf digests at `nodes`, written after them.
+int launch_upper_levels(uint8_t *nodes, uint64_t n, cudaStream_t stream, const DeviceInfo &dev) {
     uint8_t *level = nodes;
-    uint64_t n = n_leaves;
     while (n > kTopCount) {
         uint8_t *next = level + 32 * n;
         const uint64_t parents = n / 2 + (n & 1);
-        grid = persistent_grid(reinterpret_cast<const void *>(&k_merkle_level), kThreads, 0, parents, dev);
+        const uint64_t grid =
+            persistent_grid(reinterpret_cast<const void *>(&k_merkle_level), kThreads, 0, parents, dev);
         k_merkle_level<<<unsigned(grid), kThreads, 0, stream>>>(level, n, next);
         if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
         level = next;
@@ -225,6 +349,41 @@ int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_by
         if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
     }
     return KB_OK;
+}
+
+}  // namespace
+
+int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes,
+                         cudaStream_t stream, const DeviceInfo &dev) {
+    int rc = launch_leaves(buf, n_leaves, leaf_bytes, nodes, stream, dev);
+    if (rc != KB_OK) return rc;
+    return launch_upper_levels(nodes, n_leaves, stream, dev);
+}
+
+int launch_merkle_many(const uint8_t *buf, uint64_t n_trees, uint64_t leaves_per_tree, uint64_t leaf_bytes,
+                       uint8_t *roots, cudaStream_t stream, const DeviceInfo &dev) {
+    const uint64_t grid =
+        persistent_grid(reinterpret_cast<const void *>(&k_merkle_many), kThreads, 0, n_trees, dev);
+    k_merkle_many<<<unsigned(grid), kThreads, 0, stream>>>(buf, n_trees, leaves_per_tree, leaf_bytes, roots);
+    return cuda_status(cudaGetLastError());
+}
+
+uint64_t merkle_message_leaves(uint64_t len, uint64_t chunk_bytes) {
+    return len == 0 ? 1 : (len + chunk_bytes - 1) / chunk_bytes;
+}
+
+int launch_merkle_message(const uint8_t *msg, uint64_t len, uint64_t chunk_bytes, uint8_t *nodes,
+                          cudaStream_t stream, const DeviceInfo &dev) {
+    const uint64_t n = merkle_message_leaves(len, chunk_bytes);
+    const uint64_t full = len / chunk_bytes;
+    int rc = launch_leaves(msg, full, chunk_bytes, nodes, stream, dev);
+    if (rc != KB_OK) return rc;
+    if (full < n) {  // the short (or empty) last chunk
+        const uint64_t last = len - full * chunk_bytes;
+        k_merkle_leaves_any<<<1, kThreads, 0, stream>>>(msg + full * chunk_bytes, 1, last, nodes + 32 * full);
+        if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
+    }
+    return launch_upper_levels(nodes, n, stream, dev);
 }
 
 }  // namespace kb

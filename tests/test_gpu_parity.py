@@ -372,3 +372,32 @@ def test_lane_parallel_long_messages_every_variant(cuda_lib, oracle_mod, restore
     b.out_lens = np.array([DIG[v] or int(rng.choice([0, 1, 167, 168, 169, 500])) for v in b.variants],
                           dtype=np.uint32)
     assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
+
+
+@pytest.mark.parametrize("length,chunk,shift", [(0, 64, 0), (1, 64, 0), (64, 64, 0), (65, 64, 3), (1000, 136, 1),
+                                                (4097, 128, 0), (3000, 999, 5), (10_000_000, 8192, 0),
+                                                (10_000_001, 8192, 7)])
+def test_merkle_message_tree(cuda_lib, oracle_mod, length, chunk, shift):
+    torch = _torch()
+    msg = W.random_bytes(length, seed=length % 1000 + chunk)
+    raw = torch.zeros(length + shift + 8, dtype=torch.uint8, device="cuda")
+    if length:
+        raw[shift:shift + length] = dev(msg)
+    got = cuda_lib.merkle_sha3_256_message(raw.data_ptr() + shift, length, chunk)
+    assert got == oracle_mod.merkle_message_root(msg, chunk)
+
+
+@pytest.mark.parametrize("n_trees,leaves,leaf_bytes,shift", [(1, 1, 1, 0), (300, 1, 64, 0), (300, 3, 135, 1),
+                                                             (200, 7, 8, 0), (129, 13, 200, 3), (64, 33, 40, 0),
+                                                             (16, 100, 17, 5)])
+def test_merkle_many_small_trees(cuda_lib, oracle_mod, n_trees, leaves, leaf_bytes, shift):
+    torch = _torch()
+    buf = W.merkle_buffer(n_trees * leaves, leaf_bytes, seed=n_trees + leaves + leaf_bytes)
+    raw = torch.zeros(buf.size + shift + 8, dtype=torch.uint8, device="cuda")
+    raw[shift:shift + buf.size] = dev(buf)
+    roots = torch.zeros(32 * n_trees, dtype=torch.uint8, device="cuda")
+    cuda_lib.merkle_sha3_256_many(raw.data_ptr() + shift, n_trees, leaves, leaf_bytes, roots)
+    got = host(roots).reshape(n_trees, 32)
+    tree = leaves * leaf_bytes
+    for t in range(n_trees):
+        assert got[t].tobytes() == oracle_mod.merkle_root(buf[t * tree:(t + 1) * tree], leaves, leaf_bytes), t
