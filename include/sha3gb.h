@@ -325,6 +325,21 @@ int kb_server_replay(kb_server *server, const uint8_t *pool, const uint64_t *off
                      const uint8_t *variants, const uint32_t *out_lens, const int64_t *arrival_ns, uint64_t n,
                      uint8_t *outputs, int64_t *latency_ns, kb_server_stats *stats);
 
+/*
+ * keccak_p_batch -- the permutation alone, Keccak-p[b, n_r] (Section 3.1:
+ * Table 1 widths b = 25, 50, 100, 200, 400, 800, 1600; Eq. 10 rounds), applied
+ * in place to n states.  State i is 25 lanes at states + 25*i (device uint64,
+ * 8-byte aligned): lane x + 5y is word x + 5y, its bit z (Eq. 1: string bit
+ * w(5y+x)+z) is bit z of the word; for b < 1600 only the low w = b/25 bits are
+ * read and the rest are written as zero.  The n_r rounds are the last n_r of
+ * the 12 + 2l round indices (FIPS 202 Algorithm 7), so n_r = 12 + 2l gives
+ * Keccak-f[b]; n_r may exceed that (earlier, negative indices).  For
+ * reduced-round and small-width experiments; the hash entry points use
+ * Keccak-f[1600] directly.  Stream-ordered.  Bad b, n_r < 0 or n_r > 10^6:
+ * KB_ERR_INVALID; n == 0 or n_r == 0: no-op.
+ */
+int keccak_p_batch(uint64_t *states, int b, int nr, uint64_t n, void *stream);
+
 /* Synchronises `stream`, returns the device status word (KB_DEV_* bits, 0 if
  * clean) accumulated by kernels on this device since the last call, and
  * clears it.  Returns KB_ERR_CUDA if the synchronisation fails. */

@@ -67,6 +67,8 @@ _SIGS = {
     "merkle_node_count": (ctypes.c_uint64, [ctypes.c_uint64]),
     "merkle_sha3_256_levels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
                                               ctypes.c_void_p]),
+    "keccak_p_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                      ctypes.c_void_p]),
     "keccak_last_error": (ctypes.c_int, [ctypes.c_void_p]),
     "keccak_release": (None, []),
     "sha3gb_round_constants": (ctypes.c_int, [ctypes.c_void_p]),
@@ -202,6 +204,10 @@ def merkle_node_count(n_leaves: int) -> int:
 def merkle_sha3_256_levels(buf, n_leaves: int, leaf_bytes: int, nodes, stream=None) -> None:
     _check(load().merkle_sha3_256_levels(_ptr(buf), n_leaves, leaf_bytes, _ptr(nodes), _stream(stream)),
            "merkle_sha3_256_levels")
+
+
+def keccak_p_batch(states, b: int, nr: int, n: int, stream=None) -> None:
+    _check(load().keccak_p_batch(_ptr(states), b, nr, n, _stream(stream)), "keccak_p_batch")
 
 
 def keccak_last_error(stream=None) -> int:

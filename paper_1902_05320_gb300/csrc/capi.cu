@@ -293,6 +293,19 @@ int keccak_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *dige
     return launch_stream_final(states, out_lens, digests, n, static_cast<cudaStream_t>(stream), *dev);
 }
 
+int keccak_p_batch(uint64_t *states, int b, int nr, uint64_t n, void *stream) {
+    if (nr < 0 || nr > 1000000) return KB_ERR_INVALID;
+    bool width_ok = false;
+    for (int k = 0; k <= 6; ++k) width_ok = width_ok || b == 25 * (1 << k);
+    if (!width_ok) return KB_ERR_INVALID;
+    if (n == 0 || nr == 0) return KB_OK;
+    if (!states || (reinterpret_cast<uintptr_t>(states) & 7) || n > UINT64_MAX / 200) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    return launch_keccak_p(states, b, nr, n, static_cast<cudaStream_t>(stream), *dev);
+}
+
 int keccak_last_error(void *stream) {
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);

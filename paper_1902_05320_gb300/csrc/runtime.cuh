@@ -83,6 +83,7 @@ uint64_t merkle_nodes(uint64_t n_leaves);
 int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes,
                          cudaStream_t stream, const DeviceInfo &dev);
 uint64_t merkle_message_leaves(uint64_t len, uint64_t chunk_bytes);
+int launch_keccak_p(uint64_t *states, int b, int nr, uint64_t n, cudaStream_t stream, const DeviceInfo &dev);
 int launch_merkle_many(const uint8_t *buf, uint64_t n_trees, uint64_t leaves_per_tree, uint64_t leaf_bytes,
                        uint8_t *roots, cudaStream_t stream, const DeviceInfo &dev);
 int launch_merkle_message(const uint8_t *msg, uint64_t len, uint64_t chunk_bytes, uint8_t *nodes,

@@ -401,3 +401,27 @@ def test_merkle_many_small_trees(cuda_lib, oracle_mod, n_trees, leaves, leaf_byt
     tree = leaves * leaf_bytes
     for t in range(n_trees):
         assert got[t].tobytes() == oracle_mod.merkle_root(buf[t * tree:(t + 1) * tree], leaves, leaf_bytes), t
+
+
+# -- the permutation alone, every width (Keccak-p[b, n_r]) --------------------------------
+def _lanes_to_bits(lanes: np.ndarray, w: int) -> np.ndarray:
+    # Eq. 1: string bit w(5y+x)+z is bit z of lane x+5y.
+    return np.array([(int(lanes[i]) >> z) & 1 for i in range(25) for z in range(w)], dtype=np.uint8)
+
+
+@pytest.mark.parametrize("b", [25, 50, 100, 200, 400, 800, 1600])
+def test_keccak_p_every_width_and_round_count(cuda_lib, oracle_mod, b):
+    torch = _torch()
+    w = b // 25
+    l = int(np.log2(w))
+    rng = np.random.default_rng(b)
+    n = 64
+    for nr in sorted({1, 3, 12 + 2 * l, 12 + 2 * l + 5}):
+        mask = (1 << w) - 1
+        states = rng.integers(0, 2**63, size=(n, 25), dtype=np.uint64) & np.uint64(mask)
+        d = torch.from_numpy(states.view(np.int64).copy()).cuda()
+        cuda_lib.keccak_p_batch(d, b, nr, n)
+        got = d.cpu().numpy().view(np.uint64)
+        for i in range(n):
+            want = oracle_mod.keccak_p(b, nr, _lanes_to_bits(states[i], w))
+            assert np.array_equal(_lanes_to_bits(got[i], w), want), (b, nr, i)
