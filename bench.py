@@ -464,9 +464,12 @@ def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, auto
         binding.keccak_tune_set(binding.KB_TUNE_RAGGED_SCHEDULE, binding.KB_SCHEDULE_INPUT_ORDER)
         ms_in = timed()
         ref = out.clone()
+        binding.keccak_tune_set(binding.KB_TUNE_RAGGED_SCHEDULE, binding.KB_SCHEDULE_PER_VARIANT)
+        ms_pv = timed()
+        same = bool(torch.equal(ref, out))
         binding.keccak_tune_set(binding.KB_TUNE_RAGGED_SCHEDULE, binding.KB_SCHEDULE_QUEUE)
         ms_q = timed()
-        same = bool(torch.equal(ref, out))
+        same = same and bool(torch.equal(ref, out))
         tuned, ms_t = None, None
         if autotune:
             tuned = binding.keccak_batch_autotune(*d, out, b.n, stream)
@@ -475,7 +478,8 @@ def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, auto
     finally:
         for k, v in enumerate(saved):
             binding.keccak_tune_set(k, v)
-    for name, ms in (("input_order", ms_in), ("queue", ms_q), ("queue_autotuned", ms_t)):
+    for name, ms in (("input_order", ms_in), ("per_variant_launches", ms_pv), ("queue", ms_q),
+                     ("queue_autotuned", ms_t)):
         if ms is None:
             continue
         res[name] = {"ms": ms, "mhash_s": b.n / ms / 1e3, "gb_s": msg_bytes / ms / 1e6,

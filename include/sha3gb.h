@@ -367,8 +367,10 @@ void keccak_release(void);
  *     first, consumed by one persistent launch, one thread per message),
  *     KB_SCHEDULE_LANE_PARALLEL (the same order, one warp per message: the 25
  *     state lanes on 25 threads; about 2x lower latency per message at about
- *     4x the instructions, for few long messages) or KB_SCHEDULE_INPUT_ORDER
- *     (one thread per message in input order, the plain one-launch control).
+ *     4x the instructions, for few long messages), KB_SCHEDULE_PER_VARIANT (a
+ *     control: one launch per variant over that variant's messages, rate fixed
+ *     at compile time, not ordered by length) or KB_SCHEDULE_INPUT_ORDER (one
+ *     thread per message in input order, the plain one-launch control).
  *   KB_TUNE_GRAPHS: 1 (default) replays the queue schedule's launches from a
  *     CUDA graph cached per call signature (pointers, n, stream); 0 launches
  *     directly.  Work issued on the legacy default stream or on a stream that
@@ -384,6 +386,7 @@ void keccak_release(void);
 #define KB_SCHEDULE_INPUT_ORDER 0
 #define KB_SCHEDULE_QUEUE 1
 #define KB_SCHEDULE_LANE_PARALLEL 2
+#define KB_SCHEDULE_PER_VARIANT 3
 #define KB_TUNE_GRAPHS 2
 #define KB_TUNE_AUTOTUNE 3
 #define KB_TUNE_QUEUE_MIN_BLOCKS 4

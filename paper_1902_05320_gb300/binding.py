@@ -222,7 +222,7 @@ KB_TUNE_REPRESENTATION = 0
 KB_REP_PLAIN, KB_REP_INTERLEAVED = 0, 1
 KB_TUNE_RAGGED_SCHEDULE, KB_TUNE_GRAPHS, KB_TUNE_AUTOTUNE = 1, 2, 3
 KB_TUNE_QUEUE_MIN_BLOCKS, KB_TUNE_QUEUE_BLOCKS_PER_SM = 4, 5
-KB_SCHEDULE_INPUT_ORDER, KB_SCHEDULE_QUEUE, KB_SCHEDULE_LANE_PARALLEL = 0, 1, 2
+KB_SCHEDULE_INPUT_ORDER, KB_SCHEDULE_QUEUE, KB_SCHEDULE_LANE_PARALLEL, KB_SCHEDULE_PER_VARIANT = 0, 1, 2, 3
 KB_TUNE_HOST_PATH = 6
 KB_HOST_PATH_AUTO, KB_HOST_PATH_STAGED, KB_HOST_PATH_ZERO_COPY = 0, 1, 2
 

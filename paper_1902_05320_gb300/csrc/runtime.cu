@@ -110,8 +110,7 @@ int tuning_set(int key, int64_t value) {
             if (value != KB_REP_PLAIN && value != KB_REP_INTERLEAVED) return KB_ERR_INVALID;
             break;
         case KB_TUNE_RAGGED_SCHEDULE:
-            if (value != KB_SCHEDULE_INPUT_ORDER && value != KB_SCHEDULE_QUEUE && value != KB_SCHEDULE_LANE_PARALLEL)
-                return KB_ERR_INVALID;
+            if (value < KB_SCHEDULE_INPUT_ORDER || value > KB_SCHEDULE_PER_VARIANT) return KB_ERR_INVALID;
             break;
         case KB_TUNE_GRAPHS:
         case KB_TUNE_AUTOTUNE:

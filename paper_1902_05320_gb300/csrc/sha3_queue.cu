@@ -14,7 +14,9 @@
 //      message per thread.  Warps therefore run messages of nearly equal
 //      cost, and the longest messages start first so the tail is short.
 // The five operations (a memset and four kernels) are captured once per call
-// signature into a CUDA graph and replayed afterwards.
+// signature into a CUDA graph and replayed afterwards.  A control schedule
+// groups the messages by variant instead and hashes each variant with its
+// own launch (the plain per-variant form the queue is measured against).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,12 +50,21 @@ __device__ __forceinline__ uint32_t cost_bucket(uint64_t c) {
     return uint32_t(64 + (e - 6) * 8 + int((c >> (e - 3)) & 7));
 }
 
+// Bucket of a message: its cost bucket, or (for the per-variant control
+// schedule) its variant, 6 standing for an invalid one.
+template <bool BY_VARIANT>
+__device__ __forceinline__ uint32_t bucket_key(uint64_t len, int v, uint32_t dlen) {
+    if constexpr (BY_VARIANT) return v > 5 ? 6u : uint32_t(v);
+    else return cost_bucket(message_cost(len, v, dlen));
+}
+
 struct Control {
     uint32_t count[kBuckets];   // messages per bucket
     uint32_t cursor[kBuckets];  // next free slot of each bucket in the order
     unsigned long long head;    // work-queue position
 };
 
+template <bool BY_VARIANT>
 __global__ void __launch_bounds__(kScanThreads)
     k_prep(const uint64_t *__restrict__ lens, const uint8_t *__restrict__ variants,
            const uint32_t *__restrict__ out_lens, uint64_t n, uint64_t *__restrict__ tile_sums, Control *ctl) {
@@ -68,7 +79,7 @@ __global__ void __launch_bounds__(kScanThreads)
         if (i < n) {
             const uint32_t d = out_lens[i];
             s += d;
-            atomicAdd(&hist[cost_bucket(message_cost(lens[i], variants[i], d))], 1u);
+            atomicAdd(&hist[bucket_key<BY_VARIANT>(lens[i], variants[i], d)], 1u);
         }
     }
     uint64_t excl;
@@ -103,6 +114,7 @@ __global__ void __launch_bounds__(kScanThreads) k_plan(uint64_t *tile_sums, uint
     }
 }
 
+template <bool BY_VARIANT>
 __global__ void __launch_bounds__(kScanThreads)
     k_scatter(const uint64_t *__restrict__ lens, const uint8_t *__restrict__ variants,
               const uint32_t *__restrict__ out_lens, uint64_t n, const uint64_t *__restrict__ tile_sums,
@@ -122,7 +134,7 @@ __global__ void __launch_bounds__(kScanThreads)
         rank[j] = 0;
         if (i < n) {
             d[j] = out_lens[i];
-            key[j] = cost_bucket(message_cost(lens[i], variants[i], d[j]));
+            key[j] = bucket_key<BY_VARIANT>(lens[i], variants[i], d[j]);
             rank[j] = atomicAdd(&hist[key[j]], 1u);
         }
         s += d[j];
@@ -189,6 +201,34 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Per-variant control schedule: one launch per variant, each over the
+// messages of that variant (grouped by the same bucket pipeline keyed on the
+// variant), one thread per message with the variant's rate fixed at compile
+// time and no ordering by length.
+template <int V>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_sha3_variant(const uint8_t *__restrict__ msgs, const uint64_t *__restrict__ offsets,
+                   const uint64_t *__restrict__ lens, const uint32_t *__restrict__ out_lens,
+                   const uint64_t *__restrict__ out_off, const uint32_t *__restrict__ order,
+                   uint8_t *__restrict__ digests, const Control *ctl, unsigned int *status) {
+    using P = Variant<V>;
+    const uint64_t end = ctl->cursor[V], begin = end - ctl->count[V];
+    const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t k = begin + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < end; k += step) {
+        const uint32_t i = order[k];
+        const uint32_t dlen = out_lens[i];
+        if (P::digest && dlen != uint32_t(P::digest)) {
+            atomicOr(status, KB_DEV_BAD_OUTLEN);
+            continue;
+        }
+        sponge<P::rate, P::domain, false, PlainRep>(msgs + offsets[i], lens[i], digests + out_off[i], dlen);
+    }
+}
+
+__global__ void k_flag_invalid_variants(const Control *ctl, unsigned int *status) {
+    if (ctl->count[6]) atomicOr(status, KB_DEV_BAD_VARIANT);
+}
+
 // Register budgets the tuner can choose (minimum resident blocks of 128
 // threads per SM, which caps registers per thread at 65536 / (128 x MINB)).
 const int kMinBlocksChoices[] = {4, 5, 6, 8};
@@ -203,9 +243,10 @@ const void *queue_kernel(int minb) {
 }
 
 struct QueueConfig {
-    int minb = 4;           // register budget (template instance)
-    int blocks_per_sm = 0;  // 0: as many as fit
-    bool lanes = false;     // one warp per message (lane-parallel sponge)
+    int minb = 4;              // register budget (template instance)
+    int blocks_per_sm = 0;     // 0: as many as fit
+    bool lanes = false;        // one warp per message (lane-parallel sponge)
+    bool per_variant = false;  // control: one launch per variant, unsorted
 };
 
 struct Buffers {
@@ -231,6 +272,8 @@ Buffers carve(uint8_t *scratch, uint64_t n, uint64_t ntiles) {
 }
 
 uint64_t queue_grid(const QueueConfig &cfg, uint64_t n, const DeviceInfo &dev) {
+    if (cfg.per_variant)
+        return persistent_grid(reinterpret_cast<const void *>(&k_sha3_variant<1>), kThreads, 0, n, dev);
     if (cfg.lanes)
         return persistent_grid(reinterpret_cast<const void *>(&k_sha3_lanes), kThreads, 0, n * 32, dev);
     uint64_t grid = persistent_grid(queue_kernel(cfg.minb), kThreads, 0, (n + 31) / 32 * 32, dev);
@@ -244,10 +287,25 @@ int issue(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, co
           const uint32_t *out_lens, uint8_t *digests, uint64_t n, const Buffers &bf, uint64_t ntiles,
           const QueueConfig &cfg, uint64_t grid, cudaStream_t stream, const DeviceInfo &dev) {
     if (cudaMemsetAsync(bf.ctl, 0, sizeof(Control), stream) != cudaSuccess) return KB_ERR_CUDA;
-    k_prep<<<unsigned(ntiles), kScanThreads, 0, stream>>>(lens, variants, out_lens, n, bf.tile_sums, bf.ctl);
+    if (cfg.per_variant) {
+        k_prep<true><<<unsigned(ntiles), kScanThreads, 0, stream>>>(lens, variants, out_lens, n, bf.tile_sums, bf.ctl);
+        k_plan<<<1, kScanThreads, 0, stream>>>(bf.tile_sums, ntiles, bf.ctl);
+        k_scatter<true><<<unsigned(ntiles), kScanThreads, 0, stream>>>(lens, variants, out_lens, n, bf.tile_sums,
+                                                                       bf.out_off, bf.order, bf.ctl);
+        const unsigned g = unsigned(grid);
+        k_sha3_variant<0><<<g, kThreads, 0, stream>>>(msgs, offsets, lens, out_lens, bf.out_off, bf.order, digests, bf.ctl, dev.d_status);
+        k_sha3_variant<1><<<g, kThreads, 0, stream>>>(msgs, offsets, lens, out_lens, bf.out_off, bf.order, digests, bf.ctl, dev.d_status);
+        k_sha3_variant<2><<<g, kThreads, 0, stream>>>(msgs, offsets, lens, out_lens, bf.out_off, bf.order, digests, bf.ctl, dev.d_status);
+        k_sha3_variant<3><<<g, kThreads, 0, stream>>>(msgs, offsets, lens, out_lens, bf.out_off, bf.order, digests, bf.ctl, dev.d_status);
+        k_sha3_variant<4><<<g, kThreads, 0, stream>>>(msgs, offsets, lens, out_lens, bf.out_off, bf.order, digests, bf.ctl, dev.d_status);
+        k_sha3_variant<5><<<g, kThreads, 0, stream>>>(msgs, offsets, lens, out_lens, bf.out_off, bf.order, digests, bf.ctl, dev.d_status);
+        k_flag_invalid_variants<<<1, 1, 0, stream>>>(bf.ctl, dev.d_status);
+        return cuda_status(cudaGetLastError());
+    }
+    k_prep<false><<<unsigned(ntiles), kScanThreads, 0, stream>>>(lens, variants, out_lens, n, bf.tile_sums, bf.ctl);
     k_plan<<<1, kScanThreads, 0, stream>>>(bf.tile_sums, ntiles, bf.ctl);
-    k_scatter<<<unsigned(ntiles), kScanThreads, 0, stream>>>(lens, variants, out_lens, n, bf.tile_sums, bf.out_off,
-                                                             bf.order, bf.ctl);
+    k_scatter<false><<<unsigned(ntiles), kScanThreads, 0, stream>>>(lens, variants, out_lens, n, bf.tile_sums,
+                                                                    bf.out_off, bf.order, bf.ctl);
     const void *fn = cfg.lanes ? reinterpret_cast<const void *>(&k_sha3_lanes) : queue_kernel(cfg.minb);
     void *args[] = {&msgs, &offsets, &lens, &variants, &out_lens, const_cast<uint64_t **>(&bf.out_off),
                     const_cast<uint32_t **>(&bf.order), &digests, &n, const_cast<Control **>(&bf.ctl),
@@ -317,6 +375,7 @@ QueueConfig choose_config(uint64_t n, const DeviceInfo &dev) {
     if (regs > 0) cfg.minb = int(regs);
     if (bps > 0) cfg.blocks_per_sm = int(bps);
     cfg.lanes = tuning_get(KB_TUNE_RAGGED_SCHEDULE) == KB_SCHEDULE_LANE_PARALLEL;
+    cfg.per_variant = tuning_get(KB_TUNE_RAGGED_SCHEDULE) == KB_SCHEDULE_PER_VARIANT;
     return cfg;
 }
 
@@ -346,7 +405,7 @@ int launch_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const uint
     if (!graphs) return issue(msgs, offsets, lens, variants, out_lens, digests, n, bf, ntiles, cfg, grid, stream, dev);
 
     GraphKey key{{msgs, offsets, lens, variants, out_lens, digests, scratch}, n, stream,
-                 cfg.lanes ? -cfg.minb : cfg.minb, cfg.blocks_per_sm, dev.device};
+                 cfg.per_variant ? 100 : cfg.lanes ? -cfg.minb : cfg.minb, cfg.blocks_per_sm, dev.device};
     {
         std::lock_guard<std::mutex> lk(g_graph_mu);
         for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {

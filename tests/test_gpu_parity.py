@@ -303,7 +303,7 @@ def restore_tuning(cuda_lib):
         cuda_lib.keccak_tune_set(k, v)
 
 
-@pytest.mark.parametrize("schedule", [0, 1, 2])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3])
 @pytest.mark.parametrize("graphs", [0, 1])
 def test_ragged_schedules_match_oracle(cuda_lib, oracle_mod, restore_tuning, schedule, graphs):
     cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_RAGGED_SCHEDULE, schedule)
