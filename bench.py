@@ -419,6 +419,7 @@ def extra_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
     out["sha3_256_2p22_x_1KiB_mhash_s"] = n2 / ms / 1e3
     out["sha3_256_2p22_x_1KiB_gb_s"] = n2 * l2 / ms / 1e6
     del m2, d2
+    out["small_batches"] = small_batch_measurements(binding, workloads, torch, stream, rank)
     out["ragged_2p20_loguniform_0_64KiB"] = ragged_measurements(binding, workloads, torch, stream, rank)
     out["serving_poisson_200k_rps_10s"] = serving_measurements(workloads, torch, rank)
     out["merkle_4GiB_8KiB_leaves"] = merkle_measurements(binding, workloads, torch, stream, rank)
@@ -486,6 +487,29 @@ def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, auto
                      "gperm_s": total_perms / ms / 1e6}
     res["autotuned_config"] = tuned
     res["schedules_agree_bytewise"] = same
+    return res
+
+
+def small_batch_measurements(binding, workloads, torch, stream, rank) -> dict:
+    """Latency-bound single launches: 4096 x 64 B SHA3-256, and the paper's
+    own workload shape (119,040 messages of 10 bytes, the largest point of its
+    Table 3; the paper does not name the variant, SHA3-256 here)."""
+    res = {}
+    for name, n, length in (("sha3_256_4096_x_64B", 4096, 64), ("sha3_256_119040_x_10B", 119040, 10)):
+        m = torch.from_numpy(workloads.uniform_messages(n, length, seed=10 + rank)).cuda()
+        d = torch.empty(n * 32, dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            binding.keccak_batch_uniform(m, length, length, 1, 32, d, n, stream)
+        torch.cuda.synchronize()
+        reps = 50
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            binding.keccak_batch_uniform(m, length, length, 1, 32, d, n, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / reps * 1e3
+        res[name] = {"us_per_launch": us, "mhash_s": n / us, "gb_s": n * length / us / 1e3}
     return res
 
 

@@ -110,6 +110,7 @@ int keccak_batch_uniform(const uint8_t *msgs, uint64_t stride, uint64_t len, int
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("keccak_batch_uniform");
     return launch_uniform(msgs, stride, len, variant, out_len, digests, n,
                           static_cast<cudaStream_t>(stream), *dev);
 }
@@ -123,6 +124,7 @@ int keccak_batch(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *l
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("keccak_batch");
     return launch_ragged(msgs, offsets, lens, variant, out_lens, digests, n,
                          static_cast<cudaStream_t>(stream), *dev);
 }
@@ -137,6 +139,7 @@ int keccak_batch_autotune(const uint8_t *msgs, const uint64_t *offsets, const ui
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("keccak_batch_autotune");
     return autotune_ragged_queue(msgs, offsets, lens, variant, out_lens, digests, n,
                                  static_cast<cudaStream_t>(stream), *dev, chosen_min_blocks, chosen_blocks_per_sm,
                                  ms);
@@ -152,6 +155,7 @@ int merkle_sha3_256_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("merkle_sha3_256_levels");
     return launch_merkle_levels(buf, n_leaves, leaf_bytes, nodes, static_cast<cudaStream_t>(stream), *dev);
 }
 
@@ -162,6 +166,7 @@ int merkle_sha3_256(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, 
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("merkle_sha3_256");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t total = merkle_nodes(n_leaves);
     uint8_t *nodes = static_cast<uint8_t *>(stream_scratch(s, size_t(32 * total), &err));
@@ -184,6 +189,7 @@ int merkle_sha3_256_many(const uint8_t *buf, uint64_t n_trees, uint64_t leaves_p
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("merkle_sha3_256_many");
     return launch_merkle_many(buf, n_trees, leaves_per_tree, leaf_bytes, roots, static_cast<cudaStream_t>(stream),
                               *dev);
 }
@@ -195,6 +201,7 @@ int merkle_sha3_256_message(const uint8_t *msg, uint64_t len, uint64_t chunk_byt
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("merkle_sha3_256_message");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t total = merkle_nodes(n);
     uint8_t *nodes = static_cast<uint8_t *>(stream_scratch(s, size_t(32 * total), &err));
@@ -215,6 +222,7 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("keccak_batch_uniform_host");
     // In place (KB_HOST_PATH_ZERO_COPY): the kernel reads the messages and
     // writes the digests in page-locked host memory directly.  Measured slower
     // than the staged copies on GB300, so it is not the default.
@@ -269,6 +277,7 @@ int keccak_stream_init(uint8_t *states, const uint8_t *variant, uint64_t n, void
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("keccak_stream_init");
     return launch_stream_init(states, variant, n, static_cast<cudaStream_t>(stream), *dev);
 }
 
@@ -280,6 +289,7 @@ int keccak_stream_absorb(uint8_t *states, const uint8_t *msgs, const uint64_t *o
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("keccak_stream_absorb");
     return launch_stream_absorb(states, msgs, offsets, lens, n, static_cast<cudaStream_t>(stream), *dev);
 }
 
@@ -290,6 +300,7 @@ int keccak_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *dige
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("keccak_stream_final");
     return launch_stream_final(states, out_lens, digests, n, static_cast<cudaStream_t>(stream), *dev);
 }
 
@@ -303,6 +314,7 @@ int keccak_p_batch(uint64_t *states, int b, int nr, uint64_t n, void *stream) {
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
+    NvtxRange range("keccak_p_batch");
     return launch_keccak_p(states, b, nr, n, static_cast<cudaStream_t>(stream), *dev);
 }
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -11,6 +12,15 @@
 #include "../../include/sha3gb.h"
 
 namespace kb {
+
+// NVTX range for the host side of an entry point (visible in Nsight tools;
+// free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Threads per block of the thread-per-message kernels.
 constexpr int kThreads = 128;

@@ -293,6 +293,7 @@ struct Server {
             chunks += r.len ? (r.len + kGatherChunk - 1) / kGatherChunk : 1;
         }
         const uint32_t m = uint32_t(s.ids.size());
+        NvtxRange range(lanes_kernel ? "kb_server batch (long lane)" : "kb_server batch (short lane)");
         cudaError_t e = cudaMemcpyAsync(s.d_desc, s.h_desc, sizeof(ReqDesc) * m, cudaMemcpyHostToDevice, s.stream);
         if (e == cudaSuccess) {
             const uint64_t gblocks = std::min<uint64_t>(chunks, uint64_t(sm_count) * 16);
