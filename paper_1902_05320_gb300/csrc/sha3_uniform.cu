@@ -11,6 +11,9 @@
 // blocks strides over the messages.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
+
 #include "keccak_core.cuh"
 #include "keccak_interleaved.cuh"
 #include "runtime.cuh"
@@ -66,7 +69,12 @@ template <int V, int LEN, bool A8, class Rep>
 int launch_one(const uint8_t *msgs, uint64_t stride, uint64_t len, uint32_t out_len, uint8_t *digests,
                uint64_t n, cudaStream_t stream, const DeviceInfo &dev) {
     const void *fn = reinterpret_cast<const void *>(&k_sha3_uniform<V, LEN, A8, Rep>);
-    const uint64_t grid = persistent_grid(fn, kThreads, 0, n, dev);
+    // One-block messages: a grid of (occupancy x SMs) blocks strides over
+    // them.  Longer messages: one message per thread and as many blocks as
+    // that takes, so the block scheduler balances the last wave dynamically.
+    const uint64_t need = (n + kThreads - 1) / kThreads;
+    const uint64_t grid = len < uint64_t(Variant<V>::rate) ? persistent_grid(fn, kThreads, 0, n, dev)
+                                                           : std::min<uint64_t>(need, uint64_t(INT32_MAX));
     k_sha3_uniform<V, LEN, A8, Rep><<<unsigned(grid), kThreads, 0, stream>>>(msgs, stride, len, digests,
                                                                               out_len, n);
     return cuda_status(cudaGetLastError());
