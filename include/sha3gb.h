@@ -378,8 +378,8 @@ void keccak_release(void);
  *   KB_TUNE_AUTOTUNE: 1 (default) uses configurations found by
  *     keccak_batch_autotune for batches of the same size class; 0 ignores them.
  *   KB_TUNE_QUEUE_MIN_BLOCKS: register budget of the queue kernel, as the
- *     minimum resident 128-thread blocks per SM it is compiled for (4, 5, 6 or
- *     8; 0 = tuned or default 4).
+ *     minimum resident 128-thread blocks per SM it is compiled for (2, 3, 4,
+ *     5, 6 or 8; 0 = tuned or default 3).
  *   KB_TUNE_QUEUE_BLOCKS_PER_SM: blocks per SM of the persistent launch
  *     (1..32; 0 = tuned or as many as fit). */
 #define KB_TUNE_RAGGED_SCHEDULE 1

@@ -117,7 +117,7 @@ int tuning_set(int key, int64_t value) {
             if (value != 0 && value != 1) return KB_ERR_INVALID;
             break;
         case KB_TUNE_QUEUE_MIN_BLOCKS:
-            if (value != 0 && value != 4 && value != 5 && value != 6 && value != 8) return KB_ERR_INVALID;
+            if (value != 0 && (value < 2 || value > 6) && value != 8) return KB_ERR_INVALID;
             break;
         case KB_TUNE_QUEUE_BLOCKS_PER_SM:
             if (value < 0 || value > 32) return KB_ERR_INVALID;

@@ -3,8 +3,9 @@
 // lengths and variants).
 //
 // A message's cost is its number of Keccak-f permutations: floor(len/r) + 1
-// absorbed blocks plus ceil(d/r) - 1 extra squeezes.  Costs fall into 528
-// buckets (exact below 64, eight per octave above).  On the device:
+// absorbed blocks plus ceil(d/r) - 1 extra squeezes.  Costs fall into 1920
+// buckets (exact below 64, 32 per octave above, so the messages of one warp
+// differ in cost by at most 1/32).  On the device:
 //   1. k_prep: digest-offset tile sums and a bucket histogram;
 //   2. k_plan: one block scans the tile sums and lays the buckets out
 //      longest-first;
@@ -34,7 +35,8 @@
 namespace kb {
 namespace {
 
-constexpr int kBuckets = 528;
+constexpr int kBucketsPerOctave = 32;
+constexpr int kBuckets = 64 + 58 * kBucketsPerOctave;  // costs up to 2^64 - 1
 
 // Permutations a message costs (0 for an invalid variant, which the hashing
 // kernel flags and skips).
@@ -47,7 +49,7 @@ __device__ __forceinline__ uint64_t message_cost(uint64_t len, int v, uint32_t d
 __device__ __forceinline__ uint32_t cost_bucket(uint64_t c) {
     if (c < 64) return uint32_t(c);
     const int e = 63 - __clzll(static_cast<long long>(c));  // >= 6
-    return uint32_t(64 + (e - 6) * 8 + int((c >> (e - 3)) & 7));
+    return uint32_t(64 + (e - 6) * kBucketsPerOctave + int((c >> (e - 5)) & (kBucketsPerOctave - 1)));
 }
 
 // Bucket of a message: its cost bucket, or (for the per-variant control
@@ -231,10 +233,12 @@ __global__ void k_flag_invalid_variants(const Control *ctl, unsigned int *status
 
 // Register budgets the tuner can choose (minimum resident blocks of 128
 // threads per SM, which caps registers per thread at 65536 / (128 x MINB)).
-const int kMinBlocksChoices[] = {4, 5, 6, 8};
+const int kMinBlocksChoices[] = {2, 3, 4, 5, 6, 8};
 
 const void *queue_kernel(int minb) {
     switch (minb) {
+        case 2: return reinterpret_cast<const void *>(&k_sha3_queue<2>);
+        case 3: return reinterpret_cast<const void *>(&k_sha3_queue<3>);
         case 5: return reinterpret_cast<const void *>(&k_sha3_queue<5>);
         case 6: return reinterpret_cast<const void *>(&k_sha3_queue<6>);
         case 8: return reinterpret_cast<const void *>(&k_sha3_queue<8>);
@@ -243,7 +247,7 @@ const void *queue_kernel(int minb) {
 }
 
 struct QueueConfig {
-    int minb = 4;              // register budget (template instance)
+    int minb = 3;              // register budget (template instance): 3 blocks of 128 threads per SM
     int blocks_per_sm = 0;     // 0: as many as fit
     bool lanes = false;        // one warp per message (lane-parallel sponge)
     bool per_variant = false;  // control: one launch per variant, unsorted

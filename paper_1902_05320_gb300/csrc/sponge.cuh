@@ -209,27 +209,82 @@ __device__ __forceinline__ void absorb_full_rt(uint32_t (&A)[25], uint32_t (&B)[
     }
 }
 
+// Absorbs the final, padded block for a runtime rate of nwords 64-bit words:
+// rem (0 <= rem < 8*nwords) message bytes at p, the domain byte at rem and
+// 0x80 XORed into byte 8*nwords-1.  The block is read as the aligned 32-bit
+// words that hold at least one message byte, funnel-shifted into place; the
+// bytes of the last such word that lie past the message are masked off.
 template <bool A8, class Rep>
 __device__ __forceinline__ void absorb_last_rt(uint32_t (&A)[25], uint32_t (&B)[25], const uint8_t *p, uint32_t rem,
                                                int nwords, uint32_t domain) {
+    const uintptr_t start = reinterpret_cast<uintptr_t>(p);
+    const uint32_t *a = reinterpret_cast<const uint32_t *>(A8 ? start : start & ~uintptr_t(3));
+    const uint32_t sh = A8 ? 0u : uint32_t(start & 3) * 8;
+    // Aligned words 0 .. nw-1 overlap the rem message bytes.
+    const uint32_t nw = rem ? uint32_t(((start + rem - 1) >> 2) - (start >> 2)) + 1 : 0u;
+    int rb = int(8 * rem);  // message bits still to come, from the current 64-bit word on
+    uint32_t prev = nw ? __ldg(a) : 0u;
 #pragma unroll
     for (int k = 0; k < 21; ++k) {
         if (k < nwords) {
-            uint32_t lo = 0, hi = 0;
-            if (8 * k + 8 <= int(rem)) {
-                if constexpr (A8) ld_word_a8(p + 8 * k, lo, hi);
-                else ld_word_any(p + 8 * k, 8, lo, hi);
-            } else if (8 * k < int(rem)) {
-                ld_word_any(p + 8 * k, rem - 8 * k, lo, hi);
-            }
-            if (uint32_t(k) == rem / 8) {
-                const uint32_t sh = (rem % 8) * 8;
-                if (sh < 32) lo ^= domain << sh;
-                else hi ^= domain << (sh - 32);
-            }
+            const uint32_t w1 = uint32_t(2 * k + 1) < nw ? __ldg(a + 2 * k + 1) : 0u;
+            const uint32_t w2 = uint32_t(2 * k + 2) < nw ? __ldg(a + 2 * k + 2) : 0u;
+            uint32_t lo = __funnelshift_r(prev, w1, sh);
+            uint32_t hi = __funnelshift_r(w1, w2, sh);
+            prev = w2;
+            // Keep max(rb, 0) low bits (clamped to 32 per half); the domain
+            // byte goes right after the message's last bit.
+            lo &= __funnelshift_lc(0xFFFFFFFFu, 0u, uint32_t(max(rb, 0)));
+            hi &= __funnelshift_lc(0xFFFFFFFFu, 0u, uint32_t(max(rb - 32, 0)));
+            if (uint32_t(rb) < 32u) lo ^= domain << rb;
+            else if (uint32_t(rb - 32) < 32u) hi ^= domain << (rb - 32);
             if (k == nwords - 1) hi ^= 0x80000000u;
+            rb -= 64;
             Rep::xor_word(A[k], B[k], lo, hi);
         }
+    }
+}
+
+// Writes bytes [0, nbytes) of the rate part of the state (0 < nbytes <= 168)
+// to dst at any alignment.  Output byte b lands in the aligned 32-bit word
+// (b + o) / 4, o = dst mod 4, so aligned word j is a funnel shift of state
+// words j-1 and j.  Words wholly inside the output take one 32-bit store;
+// the partial words at either end are written byte by byte, so no byte
+// outside [dst, dst + nbytes) is touched.
+template <class Rep>
+__device__ __forceinline__ void squeeze_rt(const uint32_t (&A)[25], const uint32_t (&B)[25], uint8_t *dst,
+                                           uint32_t nbytes) {
+    const uintptr_t d = reinterpret_cast<uintptr_t>(dst);
+    const uint32_t o = uint32_t(d & 3);
+    uint32_t *al = reinterpret_cast<uint32_t *>(d & ~uintptr_t(3));
+    const uint32_t sh = 8 * o;
+    const uint32_t end = nbytes + o;    // output end, in bytes from al
+    const uint32_t jl = (end - 1) >> 2;  // last aligned word touched
+    const uint32_t jfull_lo = o ? 1u : 0u;
+    const uint32_t jfull_hi = (end & 3) ? jl : jl + 1;  // full words: [jfull_lo, jfull_hi)
+    uint32_t prev = 0, first = 0, last = 0;
+#pragma unroll
+    for (int j = 0; j <= 42; ++j) {
+        if (uint32_t(j) > jl) break;
+        uint32_t s = 0;
+        if (j < 42) {
+            uint32_t lo, hi;
+            Rep::get_word(A[j / 2], B[j / 2], lo, hi);
+            s = (j & 1) ? hi : lo;
+        }
+        const uint32_t v = __funnelshift_l(prev, s, sh);
+        prev = s;
+        if (uint32_t(j) >= jfull_lo && uint32_t(j) < jfull_hi) al[j] = v;
+        if (j == 0) first = v;
+        if (uint32_t(j) == jl) last = v;
+    }
+    uint8_t *b = reinterpret_cast<uint8_t *>(al);
+    if (o) {  // head: bytes o .. min(4, end) - 1 of word 0
+        const uint32_t hend = end < 4 ? end : 4u;
+        for (uint32_t i = o; i < hend; ++i) b[i] = uint8_t(first >> (8 * i));
+    }
+    if ((end & 3) && !(jl == 0 && o)) {  // tail: bytes 0 .. (end & 3) - 1 of word jl
+        for (uint32_t i = 0; i < (end & 3); ++i) b[4 * jl + i] = uint8_t(last >> (8 * i));
     }
 }
 
@@ -248,10 +303,10 @@ __device__ __forceinline__ void sponge_rt(const uint8_t *p, uint64_t len, int va
     for (uint64_t i = 0; i < total; ++i) {
         if (i < nfull) absorb_full_rt<A8, Rep>(A, B, p + i * rate, nwords);
         else if (i == nfull) absorb_last_rt<A8, Rep>(A, B, p + nfull * rate, rem, nwords, domain);
-        else squeeze<168, Rep>(A, B, dst + (i - nfull - 1) * rate, uint32_t(rate));
+        else squeeze_rt<Rep>(A, B, dst + (i - nfull - 1) * rate, uint32_t(rate));
         Rep::template permute<false>(A, B);
     }
-    squeeze<168, Rep>(A, B, dst + uint64_t(nsq) * rate, dlen - nsq * uint32_t(rate));
+    if (dlen > nsq * uint32_t(rate)) squeeze_rt<Rep>(A, B, dst + uint64_t(nsq) * rate, dlen - nsq * uint32_t(rate));
 }
 
 // One message of a ragged batch: checks its descriptor, then hashes it.

@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
         uint8_t *dst = digests + out_off[i];
         const uint32_t nsq = dlen > rate ? (dlen - 1) / rate : 0;
         for (uint32_t j = 0; j < nsq; ++j) {
-            squeeze<168, PlainRep>(A, B, dst + uint64_t(j) * rate, rate);
+            squeeze_rt<PlainRep>(A, B, dst + uint64_t(j) * rate, rate);
             PlainRep::permute<false>(A, B);
         }
-        squeeze<168, PlainRep>(A, B, dst + uint64_t(nsq) * rate, dlen - nsq * rate);
+        if (dlen > nsq * rate) squeeze_rt<PlainRep>(A, B, dst + uint64_t(nsq) * rate, dlen - nsq * rate);
         st[kDoneOff] = 1;
     }
 }

@@ -127,6 +127,21 @@ def test_ragged_every_padding_case(cuda_lib, oracle_mod):
     assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
 
 
+def test_ragged_shake_every_output_length(cuda_lib, oracle_mod):
+    # SHAKE outputs of every length 0..520 (one, two, three and four squeeze
+    # blocks), packed back to back so that the output starts fall on every
+    # alignment; message lengths cover every alignment of the last block.
+    n = 2 * 521
+    rng = np.random.default_rng(44)
+    b = W.ragged_batch(n, seed=44, lens=rng.integers(0, 400, size=n), gap=3)
+    b.variants = np.array([4 + (i & 1) for i in range(n)], dtype=np.uint8)
+    b.out_lens = np.array([i // 2 for i in range(n)], dtype=np.uint32)
+    perm = rng.permutation(n)
+    b = W.RaggedBatch(b.msgs, b.offsets[perm], b.lens[perm], b.variants[perm], b.out_lens[perm])
+    assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
+    assert cuda_lib.keccak_last_error() == 0
+
+
 def test_ragged_same_digest_alone_and_in_the_mix(cuda_lib):
     torch = _torch()
     b = W.ragged_batch(500, seed=31, max_len=4000, gap=3)
@@ -314,7 +329,7 @@ def test_ragged_schedules_match_oracle(cuda_lib, oracle_mod, restore_tuning, sch
     assert cuda_lib.keccak_last_error() == 0
 
 
-@pytest.mark.parametrize("min_blocks", [4, 5, 6, 8])
+@pytest.mark.parametrize("min_blocks", [2, 3, 4, 5, 6, 8])
 def test_queue_register_budgets_match_oracle(cuda_lib, oracle_mod, restore_tuning, min_blocks):
     cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_QUEUE_MIN_BLOCKS, min_blocks)
     cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_QUEUE_BLOCKS_PER_SM, 2)
@@ -348,7 +363,7 @@ def test_autotune_keeps_digests(cuda_lib, oracle_mod, restore_tuning):
     d = [dev(x) for x in (b.msgs, b.offsets, b.lens, b.variants, b.out_lens)]
     out = torch.zeros(b.total_out(), dtype=torch.uint8, device="cuda")
     chosen = cuda_lib.keccak_batch_autotune(*d, out, b.n)
-    assert chosen["min_blocks"] in (4, 5, 6, 8) and chosen["blocks_per_sm"] >= 1 and chosen["ms"] > 0
+    assert chosen["min_blocks"] in (2, 3, 4, 5, 6, 8) and chosen["blocks_per_sm"] >= 1 and chosen["ms"] > 0
     want = _oracle_ragged(oracle_mod, b)
     assert np.array_equal(host(out)[: b.total_out()], want)
     out.zero_()
