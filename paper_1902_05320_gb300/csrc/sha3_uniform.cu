@@ -4,8 +4,9 @@
 //
 // Specialisations: for each variant, a compile-time 64-byte message read with
 // four 16-byte loads (one rate block: the padding folds into constants and
-// round 0 runs on mostly-zero lanes), a runtime length with 8-byte aligned
-// loads, and a runtime length at any alignment.  The state representation is
+// round 0 runs on mostly-zero lanes), a runtime length below the rate (one
+// block, round 0 on zero capacity lanes), and a general runtime length; the
+// runtime forms with 8-byte aligned loads or at any alignment.  The state representation is
 // a template parameter: plain 32-bit halves by default, bit-interleaved
 // halves as the measured control for SHA3-256.  A grid of (occupancy x SMs)
 // blocks strides over the messages.
@@ -22,8 +23,9 @@
 namespace kb {
 namespace {
 
-// LEN >= 0: compile-time message length; -1: runtime.  A8: base and stride are
-// multiples of 8 (16 when LEN == 64).
+// LEN >= 0: compile-time message length; -1: runtime; -2: runtime, below the
+// rate, with at most one block of output.  A8: base and stride are multiples
+// of 8 (16 when LEN == 64).
 template <int V, int LEN, bool A8, class Rep>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     k_sha3_uniform(const uint8_t *__restrict__ msgs, uint64_t stride, uint64_t len_rt,
@@ -59,6 +61,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
                 Rep::template permute<true>(A, B);
             }
             squeeze<P::rate, Rep>(A, B, dst + uint64_t(nsq) * P::rate, dlen - nsq * P::rate);
+        } else if constexpr (LEN == -2) {
+            // A runtime length below the rate and at most one output block:
+            // the message is the padded last block and one permutation,
+            // with round 0 on the known-zero capacity lanes folded.
+            uint32_t A[25], B[25];
+#pragma unroll
+            for (int i = 0; i < 25; ++i) A[i] = B[i] = 0;
+            absorb_last<P::rate, P::domain, A8, Rep>(A, B, p, uint32_t(len));
+            Rep::template permute<true>(A, B);
+            squeeze<P::rate, Rep>(A, B, dst, dlen);
         } else {
             sponge<P::rate, P::domain, A8, Rep>(p, len, dst, dlen);
         }
@@ -95,6 +107,11 @@ int launch_variant(const uint8_t *msgs, uint64_t stride, uint64_t len, uint32_t 
         }
     }
     if (len == 64 && a16) return launch_one<V, 64, true, PlainRep>(msgs, stride, len, out_len, digests, n, stream, dev);
+    constexpr int rate = Variant<V>::rate;
+    if (len < uint64_t(rate) && (Variant<V>::digest || out_len <= uint32_t(rate))) {
+        if (a8) return launch_one<V, -2, true, PlainRep>(msgs, stride, len, out_len, digests, n, stream, dev);
+        return launch_one<V, -2, false, PlainRep>(msgs, stride, len, out_len, digests, n, stream, dev);
+    }
     if (a8) return launch_one<V, -1, true, PlainRep>(msgs, stride, len, out_len, digests, n, stream, dev);
     return launch_one<V, -1, false, PlainRep>(msgs, stride, len, out_len, digests, n, stream, dev);
 }

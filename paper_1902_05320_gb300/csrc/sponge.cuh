@@ -76,30 +76,6 @@ __device__ __forceinline__ void absorb_full(uint32_t (&A)[25], uint32_t (&B)[25]
     }
 }
 
-// Absorbs the final, padded block: rem (0 <= rem < RATE) message bytes at p,
-// then the domain byte at rem and 0x80 at RATE-1.
-template <int RATE, int DOMAIN, bool A8, class Rep>
-__device__ __forceinline__ void absorb_last(uint32_t (&A)[25], uint32_t (&B)[25], const uint8_t *p,
-                                            uint32_t rem) {
-#pragma unroll
-    for (int k = 0; k < RATE / 8; ++k) {
-        uint32_t lo = 0, hi = 0;
-        if (8 * k + 8 <= int(rem)) {
-            if constexpr (A8) ld_word_a8(p + 8 * k, lo, hi);
-            else ld_word_any(p + 8 * k, 8, lo, hi);
-        } else if (8 * k < int(rem)) {
-            ld_word_any(p + 8 * k, rem - 8 * k, lo, hi);
-        }
-        if (uint32_t(k) == rem / 8) {
-            const uint32_t sh = (rem % 8) * 8;
-            if (sh < 32) lo ^= uint32_t(DOMAIN) << sh;
-            else hi ^= uint32_t(DOMAIN) << (sh - 32);
-        }
-        if (k == RATE / 8 - 1) hi ^= 0x80000000u;
-        Rep::xor_word(A[k], B[k], lo, hi);
-    }
-}
-
 // Writes bytes [0, nbytes) of the rate part of the state to dst
 // (nbytes <= RATE), with the widest stores dst's alignment allows.
 template <int RATE, class Rep>
@@ -147,27 +123,6 @@ __device__ __forceinline__ void squeeze(const uint32_t (&A)[25], const uint32_t 
             }
         }
     }
-}
-
-// One complete sponge for a message of len bytes at p, writing dlen output
-// bytes to dst.  The permutation has a single call site, so its code appears
-// once.
-template <int RATE, int DOMAIN, bool A8, class Rep>
-__device__ __forceinline__ void sponge(const uint8_t *p, uint64_t len, uint8_t *dst, uint32_t dlen) {
-    uint32_t A[25], B[25];
-#pragma unroll
-    for (int i = 0; i < 25; ++i) A[i] = B[i] = 0;
-    const uint64_t nfull = len / RATE;
-    const uint32_t rem = uint32_t(len - nfull * RATE);
-    const uint32_t nsq = dlen > uint32_t(RATE) ? (dlen - 1) / RATE : 0;  // extra squeeze permutations
-    const uint64_t total = nfull + 1 + nsq;
-    for (uint64_t i = 0; i < total; ++i) {
-        if (i < nfull) absorb_full<RATE, A8, Rep>(A, B, p + i * RATE);
-        else if (i == nfull) absorb_last<RATE, DOMAIN, A8, Rep>(A, B, p + nfull * RATE, rem);
-        else squeeze<RATE, Rep>(A, B, dst + (i - nfull - 1) * RATE, RATE);
-        Rep::template permute<false>(A, B);
-    }
-    squeeze<RATE, Rep>(A, B, dst + uint64_t(nsq) * RATE, dlen - nsq * RATE);
 }
 
 // ---- runtime-rate sponge (ragged batches: the variant varies per message) ----
@@ -243,6 +198,34 @@ __device__ __forceinline__ void absorb_last_rt(uint32_t (&A)[25], uint32_t (&B)[
             Rep::xor_word(A[k], B[k], lo, hi);
         }
     }
+}
+
+// The final block for a compile-time rate and domain byte (one instance of
+// the runtime-rate form above, with its word loop bounds folded).
+template <int RATE, int DOMAIN, bool A8, class Rep>
+__device__ __forceinline__ void absorb_last(uint32_t (&A)[25], uint32_t (&B)[25], const uint8_t *p, uint32_t rem) {
+    absorb_last_rt<A8, Rep>(A, B, p, rem, RATE / 8, uint32_t(DOMAIN));
+}
+
+// One complete sponge for a message of len bytes at p, writing dlen output
+// bytes to dst.  The permutation has a single call site, so its code appears
+// once.
+template <int RATE, int DOMAIN, bool A8, class Rep>
+__device__ __forceinline__ void sponge(const uint8_t *p, uint64_t len, uint8_t *dst, uint32_t dlen) {
+    uint32_t A[25], B[25];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) A[i] = B[i] = 0;
+    const uint64_t nfull = len / RATE;
+    const uint32_t rem = uint32_t(len - nfull * RATE);
+    const uint32_t nsq = dlen > uint32_t(RATE) ? (dlen - 1) / RATE : 0;  // extra squeeze permutations
+    const uint64_t total = nfull + 1 + nsq;
+    for (uint64_t i = 0; i < total; ++i) {
+        if (i < nfull) absorb_full<RATE, A8, Rep>(A, B, p + i * RATE);
+        else if (i == nfull) absorb_last<RATE, DOMAIN, A8, Rep>(A, B, p + nfull * RATE, rem);
+        else squeeze<RATE, Rep>(A, B, dst + (i - nfull - 1) * RATE, RATE);
+        Rep::template permute<false>(A, B);
+    }
+    squeeze<RATE, Rep>(A, B, dst + uint64_t(nsq) * RATE, dlen - nsq * RATE);
 }
 
 // Writes bytes [0, nbytes) of the rate part of the state (0 < nbytes <= 168)
