@@ -367,7 +367,7 @@ def main() -> None:
                      "ops_per_hash": ops_perm,
                      "peak_basis": f"{SM_COUNT_GB300} SMs x {INT_LANES_PER_SM_CLK} int32 lanes/clk x "
                                    f"{SM_MAX_MHZ:.0f} MHz max SM clock",
-                     "kernel": "k_sha3_uniform<SHA3-256, 64 B>"},
+                     "kernel": "k_sha3_uniform64_tma<SHA3-256> (64-byte messages staged by bulk copies)"},
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
@@ -407,6 +407,13 @@ def extra_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
     finally:
         binding.keccak_tune_set(binding.KB_TUNE_REPRESENTATION, binding.KB_REP_PLAIN)
     out["sha3_256_2p24_x_64B_interleaved_control_mhash_s"] = n / ms / 1e3
+    # Each thread loading its own message, against the default bulk-copy staging.
+    binding.keccak_tune_set(binding.KB_TUNE_STAGING, binding.KB_STAGING_DIRECT)
+    try:
+        ms = timed(lambda: binding.keccak_batch_uniform(msgs, 64, 64, 1, 32, d32, n, stream))
+    finally:
+        binding.keccak_tune_set(binding.KB_TUNE_STAGING, binding.KB_STAGING_TMA)
+    out["sha3_256_2p24_x_64B_direct_load_control_mhash_s"] = n / ms / 1e3
     del d32
     d64 = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
     ms = timed(lambda: binding.keccak_batch_uniform(msgs, 64, 64, 3, 64, d64, n, stream))
@@ -460,7 +467,7 @@ def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, auto
         return e0.elapsed_time(e1) / reps
 
     res = {"messages": b.n, "message_bytes": msg_bytes, "permutations": total_perms}
-    saved = [binding.keccak_tune_get(k) for k in range(7)]
+    saved = [binding.keccak_tune_get(k) for k in range(8)]
     try:
         binding.keccak_tune_set(binding.KB_TUNE_RAGGED_SCHEDULE, binding.KB_SCHEDULE_INPUT_ORDER)
         ms_in = timed()
@@ -592,7 +599,8 @@ def csrc_digest() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1902_05320_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name in ("keccak_core.cuh", "keccak_interleaved.cuh", "sponge.cuh", "sha3_uniform.cu", "runtime.cuh"):
+        if name in ("keccak_core.cuh", "keccak_interleaved.cuh", "sponge.cuh", "sha3_uniform.cu", "runtime.cuh",
+                    "tma.cuh"):
             h.update(name.encode())
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]

@@ -400,6 +400,16 @@ void keccak_release(void);
 #define KB_HOST_PATH_AUTO 0
 #define KB_HOST_PATH_STAGED 1
 #define KB_HOST_PATH_ZERO_COPY 2
+/*   KB_TUNE_STAGING: how the fixed-stride kernel reads 64-byte messages packed
+ *     back to back (stride 64, 16-byte aligned, device memory) --
+ *     KB_STAGING_TMA (default: bulk asynchronous copies of 8 KiB tiles into
+ *     shared memory, two deep, then each thread reads its message from there;
+ *     measured ~0.8% faster) or KB_STAGING_DIRECT (each thread loads its
+ *     message with four 16-byte loads; the measured control).  Other shapes,
+ *     and host-mapped buffers, always load directly. */
+#define KB_TUNE_STAGING 7
+#define KB_STAGING_DIRECT 0
+#define KB_STAGING_TMA 1
 int keccak_tune_set(int key, int64_t value);
 int64_t keccak_tune_get(int key);
 

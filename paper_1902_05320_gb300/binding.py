@@ -225,6 +225,8 @@ KB_TUNE_QUEUE_MIN_BLOCKS, KB_TUNE_QUEUE_BLOCKS_PER_SM = 4, 5
 KB_SCHEDULE_INPUT_ORDER, KB_SCHEDULE_QUEUE, KB_SCHEDULE_LANE_PARALLEL, KB_SCHEDULE_PER_VARIANT = 0, 1, 2, 3
 KB_TUNE_HOST_PATH = 6
 KB_HOST_PATH_AUTO, KB_HOST_PATH_STAGED, KB_HOST_PATH_ZERO_COPY = 0, 1, 2
+KB_TUNE_STAGING = 7
+KB_STAGING_DIRECT, KB_STAGING_TMA = 0, 1
 
 
 def keccak_tune_set(key: int, value: int) -> None:

@@ -94,12 +94,13 @@ void release_device() {
 }
 
 namespace {
-constexpr int kTuneKeys = 7;
+constexpr int kTuneKeys = 8;
 // Defaults: plain layout, cost-bucketed queue, graphs on, tuned configs used,
 // register budget and blocks per SM from the tuner (or built-in defaults),
-// host buffers staged through device memory.
+// host buffers staged through device memory, packed 64-byte messages staged
+// through shared memory by bulk copies.
 std::atomic<int64_t> g_tuning[kTuneKeys] = {{KB_REP_PLAIN}, {KB_SCHEDULE_QUEUE}, {1}, {1}, {0}, {0},
-                                            {KB_HOST_PATH_AUTO}};
+                                            {KB_HOST_PATH_AUTO}, {KB_STAGING_TMA}};
 }  // namespace
 
 int64_t tuning_get(int key) { return (key >= 0 && key < kTuneKeys) ? g_tuning[key].load() : -1; }
@@ -124,6 +125,9 @@ int tuning_set(int key, int64_t value) {
             break;
         case KB_TUNE_HOST_PATH:
             if (value < KB_HOST_PATH_AUTO || value > KB_HOST_PATH_ZERO_COPY) return KB_ERR_INVALID;
+            break;
+        case KB_TUNE_STAGING:
+            if (value != KB_STAGING_DIRECT && value != KB_STAGING_TMA) return KB_ERR_INVALID;
             break;
         default:
             return KB_ERR_INVALID;

@@ -19,6 +19,7 @@
 #include "keccak_interleaved.cuh"
 #include "runtime.cuh"
 #include "sponge.cuh"
+#include "tma.cuh"
 
 namespace kb {
 namespace {
@@ -77,6 +78,101 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     }
 }
 
+// The 64-byte form with its messages staged through shared memory by bulk
+// asynchronous copies (cp.async.bulk, completed on an mbarrier): a block takes
+// tiles of kThreads consecutive messages (8 KiB, one copy issued by thread 0),
+// two buffers deep, so the next tile arrives while the current one is hashed.
+// Each thread reads its message from shared memory; once every thread has
+// read the buffer (a proxy fence, then a block barrier) thread 0 refills it
+// with the tile after next, and the hashing runs while that copy is in
+// flight.  Needs stride 64 and a 16-byte aligned base in device memory.  A
+// wait that outlasts kWaitNs sets KB_DEV_TIMEOUT; the block then waits
+// (bounded) for its copies in flight and stops without writing the rest of
+// its digests.
+constexpr uint32_t kTileBytes = kThreads * 64;  // 8 KiB
+constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s
+
+template <int V, class Rep>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_sha3_uniform64_tma(const uint8_t *__restrict__ msgs, uint8_t *__restrict__ out, uint32_t out_len, uint64_t n,
+                         unsigned int *status) {
+    using P = Variant<V>;
+    static_assert(64 < P::rate, "a 64-byte message is one block for every variant");
+    __shared__ __align__(128) uint8_t buf[2][kTileBytes];
+    __shared__ __align__(8) uint64_t bar[2];
+    const uint64_t ntiles = (n + kThreads - 1) / kThreads;
+    const uint32_t dlen = P::digest ? uint32_t(P::digest) : out_len;
+    const uint64_t stride = gridDim.x;
+    // Thread 0 issues the copies; uses[b] counts the copies issued into buffer b.
+    uint32_t uses[2] = {0, 0};
+    auto issue = [&](uint64_t tile, int b) {
+        const uint64_t first = tile * kThreads;
+        const uint32_t bytes = uint32_t(n - first < kThreads ? n - first : uint64_t(kThreads)) * 64;
+        mbar_arrive_expect_tx(&bar[b], bytes);
+        bulk_copy_g2s(buf[b], msgs + first * 64, bytes, &bar[b]);
+        ++uses[b];
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        if (blockIdx.x + stride < ntiles) issue(blockIdx.x + stride, 1);
+    }
+    uint32_t k = 0;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += stride, ++k) {
+        const int b = int(k & 1);
+        const bool ok = mbar_wait_bounded(&bar[b], (k >> 1) & 1, kWaitNs);
+        const uint64_t m = tile * kThreads + threadIdx.x;
+        uint32_t A[25], B[25];
+#pragma unroll
+        for (int i = 0; i < 25; ++i) A[i] = B[i] = 0;
+        if (ok && m < n) {
+            const uint4 *q = reinterpret_cast<const uint4 *>(buf[b] + threadIdx.x * 64);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint4 v = q[j];
+                Rep::set_word(A[2 * j], B[2 * j], v.x, v.y);
+                Rep::set_word(A[2 * j + 1], B[2 * j + 1], v.z, v.w);
+            }
+        }
+        // Every thread has read buffer b (or timed out): refill it, or stop.
+        // The proxy fence orders this thread's reads of b before the bulk
+        // copy's writes into it.
+        fence_proxy_async_smem();
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(status, KB_DEV_TIMEOUT);
+                // A buffer holds at most one copy beyond the phases consumed
+                // before this tile; wait (bounded) for it to land.
+                for (int c = 0; c < 2; ++c) {
+                    const uint32_t consumed = (k + 1 - uint32_t(c)) / 2;
+                    if (uses[c] > consumed) mbar_wait_bounded(&bar[c], consumed & 1, kWaitNs);
+                }
+            }
+            return;
+        }
+        if (threadIdx.x == 0 && tile + 2 * stride < ntiles) issue(tile + 2 * stride, b);
+        if (m < n) {
+            A[8] ^= Rep::word_a(uint64_t(P::domain));
+            B[8] ^= Rep::word_b(uint64_t(P::domain));
+            constexpr uint64_t kEnd = uint64_t(0x80) << 56;
+            A[P::rate / 8 - 1] ^= Rep::word_a(kEnd);
+            B[P::rate / 8 - 1] ^= Rep::word_b(kEnd);
+            uint8_t *dst = out + m * dlen;
+            const uint32_t nsq = dlen > uint32_t(P::rate) ? (dlen - 1) / P::rate : 0;
+            for (uint32_t i = 0; i <= nsq; ++i) {
+                if (i > 0) squeeze<P::rate, Rep>(A, B, dst + uint64_t(i - 1) * P::rate, P::rate);
+                Rep::template permute<true>(A, B);
+            }
+            squeeze<P::rate, Rep>(A, B, dst + uint64_t(nsq) * P::rate, dlen - nsq * P::rate);
+        }
+    }
+}
+
 template <int V, int LEN, bool A8, class Rep>
 int launch_one(const uint8_t *msgs, uint64_t stride, uint64_t len, uint32_t out_len, uint8_t *digests,
                uint64_t n, cudaStream_t stream, const DeviceInfo &dev) {
@@ -93,6 +189,26 @@ int launch_one(const uint8_t *msgs, uint64_t stride, uint64_t len, uint32_t out_
 }
 
 template <int V>
+int launch_tma(const uint8_t *msgs, uint32_t out_len, uint8_t *digests, uint64_t n, cudaStream_t stream,
+               const DeviceInfo &dev) {
+    const void *fn = reinterpret_cast<const void *>(&k_sha3_uniform64_tma<V, PlainRep>);
+    const uint64_t grid = persistent_grid(fn, kThreads, 0, n, dev);
+    k_sha3_uniform64_tma<V, PlainRep><<<unsigned(grid), kThreads, 0, stream>>>(msgs, digests, out_len, n,
+                                                                                 dev.d_status);
+    return cuda_status(cudaGetLastError());
+}
+
+// True when p is device memory of the current device (not host-mapped).
+bool device_resident(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice;
+}
+
+template <int V>
 int launch_variant(const uint8_t *msgs, uint64_t stride, uint64_t len, uint32_t out_len, uint8_t *digests,
                    uint64_t n, cudaStream_t stream, const DeviceInfo &dev) {
     const uintptr_t base = reinterpret_cast<uintptr_t>(msgs);
@@ -106,6 +222,8 @@ int launch_variant(const uint8_t *msgs, uint64_t stride, uint64_t len, uint32_t 
             if (a8) return launch_one<V, -1, true, InterleavedRep>(msgs, stride, len, out_len, digests, n, stream, dev);
         }
     }
+    if (len == 64 && stride == 64 && a16 && tuning_get(KB_TUNE_STAGING) == KB_STAGING_TMA && device_resident(msgs))
+        return launch_tma<V>(msgs, out_len, digests, n, stream, dev);
     if (len == 64 && a16) return launch_one<V, 64, true, PlainRep>(msgs, stride, len, out_len, digests, n, stream, dev);
     constexpr int rate = Variant<V>::rate;
     if (len < uint64_t(rate) && (Variant<V>::digest || out_len <= uint32_t(rate))) {

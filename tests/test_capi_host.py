@@ -61,14 +61,14 @@ def test_merkle_node_count(lib, oracle_mod):
 
 
 def test_tuning_knobs_validate_values(lib):
-    keys = range(7)
+    keys = range(8)
     saved = [binding.keccak_tune_get(k) for k in keys]
     try:
         assert saved[0] == binding.KB_REP_PLAIN and saved[1] == binding.KB_SCHEDULE_QUEUE
-        for key, bad in ((0, 2), (1, 4), (2, 3), (3, -1), (4, 1), (4, 7), (5, 33), (6, 3), (99, 0)):
+        for key, bad in ((0, 2), (1, 4), (2, 3), (3, -1), (4, 1), (4, 7), (5, 33), (6, 3), (7, 2), (99, 0)):
             assert lib.keccak_tune_set(key, bad) == binding.KB_ERR_INVALID
         assert binding.keccak_tune_get(99) == -1
-        for key, good in ((0, 1), (1, 0), (2, 0), (3, 0), (4, 6), (5, 3), (6, 1)):
+        for key, good in ((0, 1), (1, 0), (2, 0), (3, 0), (4, 6), (5, 3), (6, 1), (7, 1)):
             binding.keccak_tune_set(key, good)
             assert binding.keccak_tune_get(key) == good
     finally:

@@ -82,6 +82,23 @@ def test_uniform_lengths_and_alignments(cuda_lib, oracle_mod, variant):
             assert np.array_equal(got, want), (variant, L, stride, shift, out_len)
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 200, 4096 + 77, 152 * 6 * 128 * 2 + 5])
+@pytest.mark.parametrize("variant", [1, 3, 5])
+@pytest.mark.parametrize("staging", [0, 1])
+def test_uniform_64_byte_staging(cuda_lib, oracle_mod, restore_tuning, n, variant, staging):
+    # 64-byte messages back to back, loaded directly (0) and through the
+    # bulk-copy staging kernel (1): partial last tiles, one tile, and more
+    # tiles than the grid holds at once.
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_STAGING, staging)
+    out_len = DIG[variant] or 200
+    msgs = W.uniform_messages(n, 64, seed=900 + n)
+    got = gpu_uniform(cuda_lib, msgs, 64, 64, variant, out_len, n)
+    want = oracle_uniform(oracle_mod, msgs, 64, 64, variant, out_len, n)
+    bad = np.nonzero((got != want).any(axis=1))[0]
+    assert bad.size == 0, (bad.size, bad[:16])
+    assert cuda_lib.keccak_last_error() == 0
+
+
 def test_uniform_zero_stride_and_single_message(cuda_lib, oracle_mod):
     msgs = W.random_bytes(300, seed=5)
     got = gpu_uniform(cuda_lib, msgs, 0, 300, 3, 64, 37)
@@ -311,7 +328,7 @@ def test_interleaved_control_matches_oracle(cuda_lib, oracle_mod):
 # -- ragged schedules, graph replay, autotuner -------------------------------------------
 @pytest.fixture
 def restore_tuning(cuda_lib):
-    keys = range(7)
+    keys = range(8)
     saved = [cuda_lib.keccak_tune_get(k) for k in keys]
     yield
     for k, v in zip(keys, saved):
