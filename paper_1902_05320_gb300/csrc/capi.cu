@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "keccak_core.cuh"
 #include "runtime.cuh"
@@ -251,10 +252,30 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
     if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return KB_ERR_CUDA;
     int rc = cuda_status(cudaEventRecord(start, user));
     for (int s = 0; s < kStages && rc == KB_OK; ++s) rc = cuda_status(cudaStreamWaitEvent(p.streams[s], start, 0));
-    uint64_t idx = 0;
-    for (uint64_t first = 0; first < n && rc == KB_OK; first += chunk, ++idx) {
+    // Chunk sizes ramp up from chunk/16 at the start and back down at the
+    // end, so that the first copy in and the last copy out, which nothing
+    // overlaps, are short.
+    std::vector<uint64_t> counts;
+    {
+        const uint64_t base = std::max<uint64_t>(1, chunk / 16);
+        uint64_t remaining = n;
+        std::vector<uint64_t> tail;
+        for (uint64_t c = base; c < chunk && remaining; c *= 2) {
+            const uint64_t take = std::min(c, remaining);
+            counts.push_back(take);
+            remaining -= take;
+            if (!remaining) break;
+            const uint64_t take_tail = std::min(c, remaining);
+            tail.push_back(take_tail);
+            remaining -= take_tail;
+        }
+        for (; remaining; remaining -= std::min(chunk, remaining)) counts.push_back(std::min(chunk, remaining));
+        counts.insert(counts.end(), tail.rbegin(), tail.rend());
+    }
+    uint64_t first = 0;
+    for (size_t idx = 0; idx < counts.size() && rc == KB_OK; first += counts[idx], ++idx) {
         const int s = int(idx % kStages);
-        const uint64_t cnt = std::min(chunk, n - first);
+        const uint64_t cnt = counts[idx];
         const size_t span = size_t((cnt - 1) * stride + len);
         if (span) rc = cuda_status(cudaMemcpyAsync(p.d_in[s], h_msgs + first * stride, span,
                                                    cudaMemcpyHostToDevice, p.streams[s]));
