@@ -19,6 +19,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsha3gb.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "sha3gb.h")
 
+KB_SHA3_224, KB_SHA3_256, KB_SHA3_384, KB_SHA3_512, KB_SHAKE128, KB_SHAKE256 = 0, 1, 2, 3, 4, 5
 KB_OK, KB_ERR_INVALID, KB_ERR_NOMEM, KB_ERR_CUDA, KB_ERR_TIMEOUT, KB_ERR_TOO_LARGE = 0, -1, -2, -3, -4, -5
 KB_NOALLOC_MAX_MESSAGES = 65536
 KB_DEV_BAD_VARIANT, KB_DEV_BAD_OUTLEN, KB_DEV_TIMEOUT = 0x1, 0x2, 0x4
@@ -162,6 +163,7 @@ def keccak_batch_uniform_host(h_msgs, stride: int, length: int, variant: int, ou
 
 
 KB_STATE_BYTES = 384
+KB_SERVER_LONG_LANE_PARALLEL, KB_SERVER_LONG_THREAD_PER_REQUEST = 0, 1
 
 
 def keccak_stream_init(states, variants, n: int, stream=None) -> None:

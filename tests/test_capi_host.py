@@ -74,3 +74,21 @@ def test_tuning_knobs_validate_values(lib):
     finally:
         for k, v in zip(keys, saved):
             binding.keccak_tune_set(k, v)
+
+
+def test_binding_constants_match_the_header():
+    # Every numeric #define and enum value of the header, as the binding has it.
+    import os
+    import re
+
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "sha3gb.h")).read()
+    found = {}
+    for name, value in re.findall(r"#define\s+(KB_\w+)\s+(-?(?:0x[0-9a-fA-F]+|\d+))u?\b", text):
+        found[name] = int(value, 0)
+    for name, value in re.findall(r"\b(KB_\w+)\s*=\s*(-?\d+)", text):
+        found[name] = int(value)
+    assert len(found) > 30
+    missing = [k for k in found if not hasattr(binding, k)]
+    assert not missing, missing
+    wrong = {k: (v, getattr(binding, k)) for k, v in found.items() if getattr(binding, k) != v}
+    assert not wrong, wrong
