@@ -242,6 +242,8 @@ def main() -> None:
                     help="only run the Merkle measurement on LEAVES 8 KiB leaves (profiling captures)")
     ap.add_argument("--ragged-only", type=int, default=0, metavar="N",
                     help="only run the ragged-batch measurement on N messages (profiling captures)")
+    ap.add_argument("--next-only", action="store_true",
+                    help="only run the streaming, many-tree, message-tree and Keccak-p measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -272,6 +274,10 @@ def main() -> None:
     if args.ragged_only:
         print(json.dumps(ragged_measurements(binding, workloads, torch, torch.cuda.current_stream(), rank,
                                              n=args.ragged_only, autotune=False)), flush=True)
+        return
+    if args.next_only:
+        print(json.dumps(next_rows_measurements(binding, workloads, torch, torch.cuda.current_stream(), rank)),
+              flush=True)
         return
 
     n_msgs = args.messages
@@ -430,6 +436,7 @@ def extra_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
     out["ragged_2p20_loguniform_0_64KiB"] = ragged_measurements(binding, workloads, torch, stream, rank)
     out["serving_poisson_200k_rps_10s"] = serving_measurements(workloads, torch, rank)
     out["merkle_4GiB_8KiB_leaves"] = merkle_measurements(binding, workloads, torch, stream, rank)
+    out["next_rows"] = next_rows_measurements(binding, workloads, torch, stream, rank)
     try:
         out["int_lanes_per_sm_clk"] = {name: round(binding.int_issue_probe(op, 4096, stream), 2)
                                        for op, name in enumerate(("lop3", "shf", "prmt", "iadd"))}
@@ -494,6 +501,90 @@ def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, auto
                      "gperm_s": total_perms / ms / 1e6}
     res["autotuned_config"] = tuned
     res["schedules_agree_bytewise"] = same
+    return res
+
+
+def next_rows_measurements(binding, workloads, torch, stream, rank) -> dict:
+    """The rows beyond the batch hash: streaming sponge states absorbing in
+    pieces, many small Merkle trees, the tree of one long message, and the bare
+    permutation Keccak-p[b, n_r] on raw states.  Each against the integer-ALU
+    roofline where its work is whole Keccak-f[1600] permutations."""
+    peak = SM_COUNT_GB300 * INT_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    ops = ops_per_permutation()
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def rates(ms, perms, data_bytes):
+        return {"ms": ms, "gperm_s": perms / ms / 1e6, "gb_s": data_bytes / ms / 1e6,
+                "alu_frac": perms * ops / (ms / 1e3) / 1e12 / peak}
+
+    dev = lambda *shape, dtype=torch.uint8: torch.empty(*shape, dtype=dtype, device="cuda")  # noqa: E731
+    res = {}
+    # Streaming: 2^20 SHA3-256 states, init, four absorbs of 2 KiB (not a
+    # multiple of the rate, so every call leaves pending bytes), final.
+    n, piece, k = 1 << 20, 2048, 4
+    buf = torch.from_numpy(workloads.random_bytes(n * piece, seed=rank_seed(20, rank))).cuda()
+    offs = torch.arange(n, dtype=torch.int64, device="cuda") * piece
+    lens = torch.full((n,), piece, dtype=torch.int64, device="cuda")
+    states = dev(n * binding.KB_STATE_BYTES)
+    variants = torch.full((n,), 1, dtype=torch.uint8, device="cuda")
+    out_lens = torch.full((n,), 32, dtype=torch.int32, device="cuda")
+    dig = dev(n * 32)
+
+    def stream_run():
+        binding.keccak_stream_init(states, variants, n, stream)
+        for _ in range(k):
+            binding.keccak_stream_absorb(states, buf, offs, lens, n, stream)
+        binding.keccak_stream_final(states, out_lens, dig, n, stream)
+
+    ms = timed(stream_run)
+    res["stream_2p20_states_4x2KiB_sha3_256"] = rates(ms, n * (k * piece // 136 + 1), n * k * piece)
+    # The same 8 KiB per message in one call, for comparison.
+    one = dev(n * 8192)
+    for j in range(k):
+        one.view(n, 8192)[:, j * piece:(j + 1) * piece] = buf.view(n, piece)
+    ms1 = timed(lambda: binding.keccak_batch_uniform(one, 8192, 8192, 1, 32, dig, n, stream))
+    res["stream_2p20_states_4x2KiB_sha3_256"]["one_call_ms"] = ms1
+    del buf, offs, lens, states, variants, out_lens, dig, one
+    torch.cuda.empty_cache()
+    # Many small trees: 2^18 trees of 16 leaves of 256 B (one thread per tree,
+    # 3.4 waves of threads on the GPU).
+    nt, lpt, lb = 1 << 18, 16, 256
+    tb = torch.from_numpy(workloads.random_bytes(nt * lpt * lb, seed=rank_seed(21, rank))).cuda()
+    roots = dev(nt * 32)
+    ms = timed(lambda: binding.merkle_sha3_256_many(tb, nt, lpt, lb, roots, stream))
+    perms = nt * (lpt * ((1 + lb) // 136 + 1) + (lpt - 1))
+    res["merkle_many_2p18_trees_x16_x256B"] = rates(ms, perms, nt * lpt * lb)
+    del tb, roots
+    torch.cuda.empty_cache()
+    # The tree of one 1 GiB message in 8 KiB chunks.
+    length, chunk = 1 << 30, 8192
+    mb = torch.from_numpy(workloads.random_bytes(length, seed=rank_seed(22, rank))).cuda()
+    ms = timed(lambda: binding.merkle_sha3_256_message(mb, length, chunk, stream), reps=3)
+    leaves = length // chunk
+    res["merkle_message_1GiB_8KiB_chunks"] = rates(ms, leaves * ((1 + chunk) // 136 + 1) + leaves - 1, length)
+    del mb
+    torch.cuda.empty_cache()
+    # The bare permutation on 2^24 raw 200-byte states.
+    ns = 1 << 24
+    st = torch.from_numpy(workloads.random_bytes(ns * 200, seed=rank_seed(23, rank))).cuda().view(torch.int64)
+    for b, nr in ((1600, 24), (1600, 12), (200, 18)):
+        ms = timed(lambda: binding.keccak_p_batch(st, b, nr, ns, stream))
+        r = {"ms": ms, "gstates_s": ns / ms / 1e6, "hbm_gb_s": ns * 400 / ms / 1e6}
+        if b == 1600 and nr == 24:
+            r["alu_frac"] = ns * ops / (ms / 1e3) / 1e12 / peak
+        res[f"keccak_p_{b}_{nr}_2p24_states"] = r
+    del st
+    torch.cuda.empty_cache()
     return res
 
 

@@ -37,47 +37,55 @@ __device__ __forceinline__ void prefixed_word(uint32_t &carry, uint32_t lo, uint
 }
 
 // Leaves at 8-byte aligned addresses with leaf_bytes % 8 == 0.
+// The state after absorbing 0x00 || leaf (leaf_bytes bytes at p, both
+// multiples of 8) and its padding, permuted: SHA3-256 of the prefixed leaf
+// sits in lanes 0..3.  The prefix byte is shifted in through one-byte funnel
+// shifts of the leaf's aligned 8-byte words.
+__device__ __forceinline__ void leaf_state_a8(const uint8_t *p, uint64_t leaf_bytes, uint32_t (&A)[25],
+                                              uint32_t (&B)[25]) {
+    const uint64_t mwords = leaf_bytes / 8;  // leaf words
+    const uint64_t vlen = leaf_bytes + 1;    // prefixed message length
+    const uint64_t nfull = vlen / kRate;
+    const uint32_t rem = uint32_t(vlen - nfull * kRate);
+#pragma unroll
+    for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
+    uint32_t carry = 0x00u << 24;  // leaf prefix byte
+    for (uint64_t b = 0; b <= nfull; ++b) {
+        const uint64_t g0 = b * (kRate / 8);
+        if (b < nfull) {
+#pragma unroll
+            for (int k = 0; k < kRate / 8; ++k) {
+                uint32_t lo, hi, vlo, vhi;
+                ld_word_a8(p + 8 * (g0 + k), lo, hi);
+                prefixed_word(carry, lo, hi, vlo, vhi);
+                PlainRep::xor_word(A[k], B[k], vlo, vhi);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kRate / 8; ++k) {
+                uint32_t lo = 0, hi = 0, vlo, vhi;
+                if (g0 + k < mwords) ld_word_a8(p + 8 * (g0 + k), lo, hi);
+                prefixed_word(carry, lo, hi, vlo, vhi);
+                if (uint32_t(k) == rem / 8) {
+                    const uint32_t sh = (rem % 8) * 8;
+                    if (sh < 32) vlo ^= uint32_t(kDomain) << sh;
+                    else vhi ^= uint32_t(kDomain) << (sh - 32);
+                }
+                if (k == kRate / 8 - 1) vhi ^= 0x80000000u;
+                PlainRep::xor_word(A[k], B[k], vlo, vhi);
+            }
+        }
+        PlainRep::permute<false>(A, B);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     k_merkle_leaves_a8(const uint8_t *__restrict__ buf, uint64_t n_leaves, uint64_t leaf_bytes,
                        uint8_t *__restrict__ out) {
     const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
-    const uint64_t mwords = leaf_bytes / 8;          // leaf words
-    const uint64_t vlen = leaf_bytes + 1;            // prefixed message length
-    const uint64_t nfull = vlen / kRate;
-    const uint32_t rem = uint32_t(vlen - nfull * kRate);
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n_leaves; i += step) {
-        const uint8_t *p = buf + i * leaf_bytes;
         uint32_t A[25], B[25];
-#pragma unroll
-        for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
-        uint32_t carry = 0x00u << 24;  // leaf prefix byte
-        for (uint64_t b = 0; b <= nfull; ++b) {
-            const uint64_t g0 = b * (kRate / 8);
-            if (b < nfull) {
-#pragma unroll
-                for (int k = 0; k < kRate / 8; ++k) {
-                    uint32_t lo, hi, vlo, vhi;
-                    ld_word_a8(p + 8 * (g0 + k), lo, hi);
-                    prefixed_word(carry, lo, hi, vlo, vhi);
-                    PlainRep::xor_word(A[k], B[k], vlo, vhi);
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kRate / 8; ++k) {
-                    uint32_t lo = 0, hi = 0, vlo, vhi;
-                    if (g0 + k < mwords) ld_word_a8(p + 8 * (g0 + k), lo, hi);
-                    prefixed_word(carry, lo, hi, vlo, vhi);
-                    if (uint32_t(k) == rem / 8) {
-                        const uint32_t sh = (rem % 8) * 8;
-                        if (sh < 32) vlo ^= uint32_t(kDomain) << sh;
-                        else vhi ^= uint32_t(kDomain) << (sh - 32);
-                    }
-                    if (k == kRate / 8 - 1) vhi ^= 0x80000000u;
-                    PlainRep::xor_word(A[k], B[k], vlo, vhi);
-                }
-            }
-            PlainRep::permute<false>(A, B);
-        }
+        leaf_state_a8(buf + i * leaf_bytes, leaf_bytes, A, B);
         squeeze<kRate, PlainRep>(A, B, out + 32 * i, 32);
     }
 }
@@ -268,6 +276,7 @@ constexpr int kStackDepth = 40;
 // order; equal-size subtrees on the stack merge at once, and the remaining
 // ones merge right to left at the end, which builds exactly the level-by-
 // level tree with odd nodes carried up.
+template <bool A8>
 __global__ void __launch_bounds__(kThreads)
     k_merkle_many(const uint8_t *__restrict__ buf, uint64_t n_trees, uint64_t leaves_per_tree, uint64_t leaf_bytes,
                   uint8_t *__restrict__ roots) {
@@ -278,7 +287,17 @@ __global__ void __launch_bounds__(kThreads)
         int top = 0;
         for (uint64_t i = 0; i < leaves_per_tree; ++i) {
             uint32_t d[8];
-            leaf_digest(buf + (t * leaves_per_tree + i) * leaf_bytes, leaf_bytes, d);
+            if constexpr (A8) {
+                uint32_t A[25], B[25];
+                leaf_state_a8(buf + (t * leaves_per_tree + i) * leaf_bytes, leaf_bytes, A, B);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    d[2 * k] = A[k];
+                    d[2 * k + 1] = B[k];
+                }
+            } else {
+                leaf_digest(buf + (t * leaves_per_tree + i) * leaf_bytes, leaf_bytes, d);
+            }
             uint64_t sz = 1;
             while (top > 0 && size[top - 1] == sz) {
                 uint32_t l[8];
@@ -367,9 +386,18 @@ int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_by
 
 int launch_merkle_many(const uint8_t *buf, uint64_t n_trees, uint64_t leaves_per_tree, uint64_t leaf_bytes,
                        uint8_t *roots, cudaStream_t stream, const DeviceInfo &dev) {
-    const uint64_t grid =
-        persistent_grid(reinterpret_cast<const void *>(&k_merkle_many), kThreads, 0, n_trees, dev);
-    k_merkle_many<<<unsigned(grid), kThreads, 0, stream>>>(buf, n_trees, leaves_per_tree, leaf_bytes, roots);
+    // Leaves on 8-byte boundaries (buffer and leaf size) take the aligned
+    // 8-byte loads; others the byte-exact reads.
+    const bool a8 = ((reinterpret_cast<uintptr_t>(buf) | leaf_bytes) & 7) == 0;
+    const void *fn = a8 ? reinterpret_cast<const void *>(&k_merkle_many<true>)
+                        : reinterpret_cast<const void *>(&k_merkle_many<false>);
+    const uint64_t grid = persistent_grid(fn, kThreads, 0, n_trees, dev);
+    if (a8)
+        k_merkle_many<true><<<unsigned(grid), kThreads, 0, stream>>>(buf, n_trees, leaves_per_tree, leaf_bytes,
+                                                                      roots);
+    else
+        k_merkle_many<false><<<unsigned(grid), kThreads, 0, stream>>>(buf, n_trees, leaves_per_tree, leaf_bytes,
+                                                                       roots);
     return cuda_status(cudaGetLastError());
 }
 

@@ -421,7 +421,8 @@ def test_merkle_message_tree(cuda_lib, oracle_mod, length, chunk, shift):
 
 @pytest.mark.parametrize("n_trees,leaves,leaf_bytes,shift", [(1, 1, 1, 0), (300, 1, 64, 0), (300, 3, 135, 1),
                                                              (200, 7, 8, 0), (129, 13, 200, 3), (64, 33, 40, 0),
-                                                             (16, 100, 17, 5)])
+                                                             (16, 100, 17, 5), (32, 16, 256, 0),
+                                                             (50, 5, 1000, 0), (40, 2, 136, 0)])
 def test_merkle_many_small_trees(cuda_lib, oracle_mod, n_trees, leaves, leaf_bytes, shift):
     torch = _torch()
     buf = W.merkle_buffer(n_trees * leaves, leaf_bytes, seed=n_trees + leaves + leaf_bytes)
