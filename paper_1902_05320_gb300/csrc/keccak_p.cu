@@ -68,7 +68,7 @@ __device__ __forceinline__ void small_round(uint32_t (&A)[25], int ir) {
         for (int x = 0; x < 5; ++x)
             A[x + 5 * y] = chi3(Bv[x + 5 * y], Bv[(x + 1) % 5 + 5 * y], Bv[(x + 2) % 5 + 5 * y]);
     constexpr uint32_t mask = W == 32 ? 0xffffffffu : ((1u << W) - 1u);
-    A[0] ^= uint32_t(c_rc255.v[((ir % 255) + 255) % 255]) & mask;
+    A[0] ^= uint32_t(c_rc255.v[ir]) & mask;
 }
 
 template <int W>
@@ -80,15 +80,39 @@ __global__ void __launch_bounds__(kThreads) k_keccak_p_small(uint64_t *states, i
         uint32_t A[25];
 #pragma unroll
         for (int k = 0; k < 25; ++k) A[k] = uint32_t(s[k] & mask);
-        for (int r = 0; r < nr; ++r) small_round<W>(A, first_ir + r);
+        int ir = ((first_ir % 255) + 255) % 255;  // rc has period 255 (Algorithm 5)
+        for (int r = 0; r < nr; ++r) {
+            small_round<W>(A, ir);
+            ir = ir == 254 ? 0 : ir + 1;
+        }
 #pragma unroll
         for (int k = 0; k < 25; ++k) s[k] = A[k];
     }
 }
 
-// Width 64: the plain 32-bit-half round of the hashing kernels.
+// One round of Keccak-p[1600] (Eq. 10) with round-constant index ir of the
+// period-255 table, in place.
+__device__ __forceinline__ void p1600_round(uint32_t (&L)[25], uint32_t (&H)[25], int ir) {
+    uint32_t NL[25], NH[25];
+    plain_round_body(L, H, NL, NH);
+    const uint64_t rc = c_rc255.v[ir];
+    NL[0] ^= uint32_t(rc);
+    NH[0] ^= uint32_t(rc >> 32);
+#pragma unroll
+    for (int k = 0; k < 25; ++k) {
+        L[k] = NL[k];
+        H[k] = NH[k];
+    }
+}
+
+// Width 64: the plain 32-bit-half round of the hashing kernels.  Keccak-f[1600]
+// itself (first_ir 0, 24 rounds) runs the hashing kernels' permutation;
+// other round ranges run four rounds per loop pass, so that the compiler
+// renames the state between rounds instead of copying it.
 __global__ void __launch_bounds__(kThreads) k_keccak_p_1600(uint64_t *states, int first_ir, int nr, uint64_t n) {
     const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
+    const bool full = first_ir == 0 && nr == 24;
+    const int ir0 = ((first_ir % 255) + 255) % 255;  // rc has period 255 (Algorithm 5)
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += step) {
         uint2 *s = reinterpret_cast<uint2 *>(states + 25 * i);
         uint32_t L[25], H[25];
@@ -98,16 +122,21 @@ __global__ void __launch_bounds__(kThreads) k_keccak_p_1600(uint64_t *states, in
             L[k] = v.x;
             H[k] = v.y;
         }
-        for (int r = 0; r < nr; ++r) {
-            uint32_t NL[25], NH[25];
-            plain_round_body(L, H, NL, NH);
-            const uint64_t rc = c_rc255.v[(((first_ir + r) % 255) + 255) % 255];
-            NL[0] ^= uint32_t(rc);
-            NH[0] ^= uint32_t(rc >> 32);
+        if (full) {
+            keccak_f1600_plain<false>(L, H);
+        } else {
+            int ir = ir0, r = 0;
+#pragma unroll 1
+            for (; r + 4 <= nr; r += 4) {
 #pragma unroll
-            for (int k = 0; k < 25; ++k) {
-                L[k] = NL[k];
-                H[k] = NH[k];
+                for (int j = 0; j < 4; ++j) {
+                    p1600_round(L, H, ir);
+                    ir = ir == 254 ? 0 : ir + 1;
+                }
+            }
+            for (; r < nr; ++r) {
+                p1600_round(L, H, ir);
+                ir = ir == 254 ? 0 : ir + 1;
             }
         }
 #pragma unroll

@@ -37,44 +37,52 @@ __device__ __forceinline__ void prefixed_word(uint32_t &carry, uint32_t lo, uint
 }
 
 // Leaves at 8-byte aligned addresses with leaf_bytes % 8 == 0.
-// The state after absorbing 0x00 || leaf (leaf_bytes bytes at p, both
-// multiples of 8) and its padding, permuted: SHA3-256 of the prefixed leaf
-// sits in lanes 0..3.  The prefix byte is shifted in through one-byte funnel
-// shifts of the leaf's aligned 8-byte words.
+// XORs block b of the padded message 0x00 || leaf (leaf_bytes bytes at p,
+// mwords = leaf_bytes / 8 words, nfull full blocks, rem bytes in the last)
+// into the state.  The prefix byte is shifted in through one-byte funnel
+// shifts of the leaf's aligned 8-byte words; carry holds the byte carried
+// between words (0 before block 0).
+__device__ __forceinline__ void absorb_leaf_block_a8(uint32_t (&A)[25], uint32_t (&B)[25], const uint8_t *p,
+                                                     uint64_t b, uint64_t nfull, uint32_t rem, uint64_t mwords,
+                                                     uint32_t &carry) {
+    const uint64_t g0 = b * (kRate / 8);
+    if (b < nfull) {
+#pragma unroll
+        for (int k = 0; k < kRate / 8; ++k) {
+            uint32_t lo, hi, vlo, vhi;
+            ld_word_a8(p + 8 * (g0 + k), lo, hi);
+            prefixed_word(carry, lo, hi, vlo, vhi);
+            PlainRep::xor_word(A[k], B[k], vlo, vhi);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRate / 8; ++k) {
+            uint32_t lo = 0, hi = 0, vlo, vhi;
+            if (g0 + k < mwords) ld_word_a8(p + 8 * (g0 + k), lo, hi);
+            prefixed_word(carry, lo, hi, vlo, vhi);
+            if (uint32_t(k) == rem / 8) {
+                const uint32_t sh = (rem % 8) * 8;
+                if (sh < 32) vlo ^= uint32_t(kDomain) << sh;
+                else vhi ^= uint32_t(kDomain) << (sh - 32);
+            }
+            if (k == kRate / 8 - 1) vhi ^= 0x80000000u;
+            PlainRep::xor_word(A[k], B[k], vlo, vhi);
+        }
+    }
+}
+
+// The state after absorbing 0x00 || leaf and its padding, permuted:
+// SHA3-256 of the prefixed leaf sits in lanes 0..3.
 __device__ __forceinline__ void leaf_state_a8(const uint8_t *p, uint64_t leaf_bytes, uint32_t (&A)[25],
                                               uint32_t (&B)[25]) {
-    const uint64_t mwords = leaf_bytes / 8;  // leaf words
-    const uint64_t vlen = leaf_bytes + 1;    // prefixed message length
+    const uint64_t vlen = leaf_bytes + 1;  // prefixed message length
     const uint64_t nfull = vlen / kRate;
     const uint32_t rem = uint32_t(vlen - nfull * kRate);
 #pragma unroll
     for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
     uint32_t carry = 0x00u << 24;  // leaf prefix byte
     for (uint64_t b = 0; b <= nfull; ++b) {
-        const uint64_t g0 = b * (kRate / 8);
-        if (b < nfull) {
-#pragma unroll
-            for (int k = 0; k < kRate / 8; ++k) {
-                uint32_t lo, hi, vlo, vhi;
-                ld_word_a8(p + 8 * (g0 + k), lo, hi);
-                prefixed_word(carry, lo, hi, vlo, vhi);
-                PlainRep::xor_word(A[k], B[k], vlo, vhi);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < kRate / 8; ++k) {
-                uint32_t lo = 0, hi = 0, vlo, vhi;
-                if (g0 + k < mwords) ld_word_a8(p + 8 * (g0 + k), lo, hi);
-                prefixed_word(carry, lo, hi, vlo, vhi);
-                if (uint32_t(k) == rem / 8) {
-                    const uint32_t sh = (rem % 8) * 8;
-                    if (sh < 32) vlo ^= uint32_t(kDomain) << sh;
-                    else vhi ^= uint32_t(kDomain) << (sh - 32);
-                }
-                if (k == kRate / 8 - 1) vhi ^= 0x80000000u;
-                PlainRep::xor_word(A[k], B[k], vlo, vhi);
-            }
-        }
+        absorb_leaf_block_a8(A, B, p, b, nfull, rem, leaf_bytes / 8, carry);
         PlainRep::permute<false>(A, B);
     }
 }
@@ -200,53 +208,42 @@ __global__ void __launch_bounds__(kTopThreads) k_merkle_top(uint8_t *level, uint
 
 // ---- many small trees, one thread per tree ----------------------------------
 
-// SHA3-256(0x00 || leaf) of leaf_bytes bytes at p (any alignment), as the
-// eight little-endian 32-bit words of the digest.
-__device__ __forceinline__ void leaf_digest(const uint8_t *p, uint64_t leaf_bytes, uint32_t (&d)[8]) {
-    const uint64_t vlen = leaf_bytes + 1;
-    const uint64_t nfull = vlen / kRate;
-    const uint32_t rem = uint32_t(vlen - nfull * kRate);
-    uint32_t A[25], B[25];
+// XORs block b of the padded message 0x00 || leaf (leaf_bytes bytes at p, any
+// alignment; nfull full blocks, rem bytes in the last) into the state,
+// reading the leaf byte-exactly.
+__device__ __forceinline__ void absorb_leaf_block_any(uint32_t (&A)[25], uint32_t (&B)[25], const uint8_t *p,
+                                                      uint64_t b, uint64_t nfull, uint32_t rem) {
+    const uint32_t valid = b < nfull ? uint32_t(kRate) : rem;
 #pragma unroll
-    for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
-    for (uint64_t b = 0; b <= nfull; ++b) {
-        const uint32_t valid = b < nfull ? uint32_t(kRate) : rem;
-#pragma unroll
-        for (int k = 0; k < kRate / 8; ++k) {
-            const uint64_t v0 = b * kRate + 8 * k;  // virtual bytes [v0, v0+8) = leaf bytes [v0-1, v0+7)
-            uint32_t lo = 0, hi = 0;
-            if (uint32_t(8 * k) < valid) {
-                const uint32_t nv = valid - 8 * k < 8 ? valid - 8 * k : 8;
-                if (v0 == 0) {
-                    if (nv > 1) ld_word_any(p, nv - 1, lo, hi);
-                    hi = __funnelshift_l(lo, hi, 8);
-                    lo = lo << 8;  // prefix byte 0x00
-                } else {
-                    ld_word_any(p + (v0 - 1), nv, lo, hi);
-                }
+    for (int k = 0; k < kRate / 8; ++k) {
+        const uint64_t v0 = b * kRate + 8 * k;  // virtual bytes [v0, v0+8) = leaf bytes [v0-1, v0+7)
+        uint32_t lo = 0, hi = 0;
+        if (uint32_t(8 * k) < valid) {
+            const uint32_t nv = valid - 8 * k < 8 ? valid - 8 * k : 8;
+            if (v0 == 0) {
+                if (nv > 1) ld_word_any(p, nv - 1, lo, hi);
+                hi = __funnelshift_l(lo, hi, 8);
+                lo = lo << 8;  // prefix byte 0x00
+            } else {
+                ld_word_any(p + (v0 - 1), nv, lo, hi);
             }
-            if (b == nfull) {
-                if (uint32_t(k) == rem / 8) {
-                    const uint32_t sh = (rem % 8) * 8;
-                    if (sh < 32) lo ^= uint32_t(kDomain) << sh;
-                    else hi ^= uint32_t(kDomain) << (sh - 32);
-                }
-                if (k == kRate / 8 - 1) hi ^= 0x80000000u;
-            }
-            PlainRep::xor_word(A[k], B[k], lo, hi);
         }
-        PlainRep::permute<false>(A, B);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        d[2 * k] = A[k];
-        d[2 * k + 1] = B[k];
+        if (b == nfull) {
+            if (uint32_t(k) == rem / 8) {
+                const uint32_t sh = (rem % 8) * 8;
+                if (sh < 32) lo ^= uint32_t(kDomain) << sh;
+                else hi ^= uint32_t(kDomain) << (sh - 32);
+            }
+            if (k == kRate / 8 - 1) hi ^= 0x80000000u;
+        }
+        PlainRep::xor_word(A[k], B[k], lo, hi);
     }
 }
 
-// SHA3-256(0x01 || left || right) from digests held as words.
-__device__ __forceinline__ void node_digest(const uint32_t (&l)[8], const uint32_t (&r)[8], uint32_t (&d)[8]) {
-    uint32_t A[25], B[25];
+// The state holding the padded block of 0x01 || left || right (digests as
+// eight little-endian 32-bit words each), ready to permute.
+__device__ __forceinline__ void load_node_block(uint32_t (&A)[25], uint32_t (&B)[25], const uint32_t (&l)[8],
+                                                const uint32_t (&r)[8]) {
 #pragma unroll
     for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
     uint32_t carry = 0x01u << 24;  // node prefix byte
@@ -260,12 +257,6 @@ __device__ __forceinline__ void node_digest(const uint32_t (&l)[8], const uint32
     }
     PlainRep::set_word(A[8], B[8], (carry >> 24) | (uint32_t(kDomain) << 8), 0u);
     B[kRate / 8 - 1] ^= 0x80000000u;
-    PlainRep::permute<true>(A, B);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        d[2 * k] = A[k];
-        d[2 * k + 1] = B[k];
-    }
 }
 
 // Stack of subtree digests: sizes are distinct powers of two (the binary
@@ -275,54 +266,88 @@ constexpr int kStackDepth = 40;
 // Tree t = leaves [t*L, (t+1)*L) of leaf_bytes each.  Leaves are hashed in
 // order; equal-size subtrees on the stack merge at once, and the remaining
 // ones merge right to left at the end, which builds exactly the level-by-
-// level tree with odd nodes carried up.
+// level tree with odd nodes carried up.  Every leaf block and every node is
+// one pass of a single loop around one permutation call site, so the kernel
+// holds one copy of the permutation's code.
 template <bool A8>
 __global__ void __launch_bounds__(kThreads)
     k_merkle_many(const uint8_t *__restrict__ buf, uint64_t n_trees, uint64_t leaves_per_tree, uint64_t leaf_bytes,
                   uint8_t *__restrict__ roots) {
     const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t vlen = leaf_bytes + 1;
+    const uint64_t nfull = vlen / kRate;
+    const uint32_t rem = uint32_t(vlen - nfull * kRate);
+    enum Mode { kLeaf, kMerge, kFold };
     for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n_trees; t += step) {
         uint32_t stack[kStackDepth][8];
         uint64_t size[kStackDepth];
         int top = 0;
-        for (uint64_t i = 0; i < leaves_per_tree; ++i) {
-            uint32_t d[8];
-            if constexpr (A8) {
-                uint32_t A[25], B[25];
-                leaf_state_a8(buf + (t * leaves_per_tree + i) * leaf_bytes, leaf_bytes, A, B);
+        uint32_t cur[8];  // the digest being merged or folded
+        uint32_t A[25], B[25];
+        uint64_t leaf = 0, blk = 0, sz = 0;
+        uint32_t carry = 0;
+        int j = 0;  // fold position
+        Mode mode = kLeaf;
+        const uint8_t *first_leaf = buf + t * leaves_per_tree * leaf_bytes;
+        for (;;) {
+            if (mode == kLeaf) {
+                const uint8_t *p = first_leaf + leaf * leaf_bytes;
+                if (blk == 0) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    d[2 * k] = A[k];
-                    d[2 * k + 1] = B[k];
+                    for (int k = 0; k < 25; ++k) A[k] = B[k] = 0;
+                    carry = 0x00u << 24;  // leaf prefix byte
                 }
+                if constexpr (A8) absorb_leaf_block_a8(A, B, p, blk, nfull, rem, leaf_bytes / 8, carry);
+                else absorb_leaf_block_any(A, B, p, blk, nfull, rem);
             } else {
-                leaf_digest(buf + (t * leaves_per_tree + i) * leaf_bytes, leaf_bytes, d);
-            }
-            uint64_t sz = 1;
-            while (top > 0 && size[top - 1] == sz) {
                 uint32_t l[8];
+                const int li = mode == kMerge ? top - 1 : j;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) l[k] = stack[top - 1][k];
-                node_digest(l, d, d);
+                for (int k = 0; k < 8; ++k) l[k] = stack[li][k];
+                load_node_block(A, B, l, cur);
+            }
+            PlainRep::permute<false>(A, B);
+            if (mode == kLeaf && blk < nfull) {
+                ++blk;
+                continue;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                cur[2 * k] = A[k];
+                cur[2 * k + 1] = B[k];
+            }
+            if (mode == kFold) {
+                if (j == 0) break;  // cur is the root
+                --j;
+                continue;
+            }
+            if (mode == kLeaf) {
+                sz = 1;
+                blk = 0;
+                ++leaf;
+            } else {  // kMerge: cur = node(stack[top - 1], cur)
                 sz *= 2;
                 --top;
             }
+            if (top > 0 && size[top - 1] == sz) {
+                mode = kMerge;
+                continue;
+            }
+            if (leaf < leaves_per_tree) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) stack[top][k] = d[k];
-            size[top++] = sz;
-        }
-        uint32_t acc[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = stack[top - 1][k];
-        for (int j = top - 2; j >= 0; --j) {
-            uint32_t l[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) l[k] = stack[j][k];
-            node_digest(l, acc, acc);
+                for (int k = 0; k < 8; ++k) stack[top][k] = cur[k];
+                size[top++] = sz;
+                mode = kLeaf;
+                continue;
+            }
+            // All leaves are in: fold the stack's subtrees into cur, right to left.
+            if (top == 0) break;  // cur is the root
+            j = top - 1;
+            mode = kFold;
         }
         uint4 *o = reinterpret_cast<uint4 *>(roots + 32 * t);
-        o[0] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
-        o[1] = make_uint4(acc[4], acc[5], acc[6], acc[7]);
+        o[0] = make_uint4(cur[0], cur[1], cur[2], cur[3]);
+        o[1] = make_uint4(cur[4], cur[5], cur[6], cur[7]);
     }
 }
 
