@@ -165,19 +165,24 @@ def cpu_baseline(msgs: np.ndarray, seconds: float = 8.0) -> dict:
     oracle.build()
     cores = len(os.sched_getaffinity(0))
 
-    def run(k):
+    def run(k, threads):
         offs = np.arange(k, dtype=np.uint64) * np.uint64(MSG_BYTES)
         t = time.perf_counter()
         oracle.hash_batch(msgs[: k * MSG_BYTES], offs, np.full(k, MSG_BYTES, np.uint64),
-                          np.full(k, VARIANT, np.uint8), np.full(k, DIGEST, np.uint32), cores)
+                          np.full(k, VARIANT, np.uint8), np.full(k, DIGEST, np.uint32), threads)
         return time.perf_counter() - t
 
     k0 = 64 * cores
-    dt0 = run(k0)
+    dt0 = run(k0, cores)
     k = int(min(N_MSGS, max(k0, k0 * seconds / max(dt0, 1e-6))))
-    dt = run(k)
+    dt = run(k, cores)
+    # The same on one host thread, for a per-core figure (a shorter sample).
+    k1 = max(64, k // (4 * cores))
+    dt1 = run(k1, 1)
     return {"value": k / dt / 1e6, "unit": "Mhash/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {k} of the 2^24 64-byte messages, SHA3-256, {dt:.1f} s on {cores} host threads"}
+            "sample": f"first {k} of the 2^24 64-byte messages, SHA3-256, {dt:.1f} s on {cores} host threads",
+            "single_core_value": k1 / dt1 / 1e6,
+            "single_core_sample": f"first {k1} of the same messages, {dt1:.1f} s on 1 host thread"}
 
 
 def run_reference(args) -> None:
