@@ -198,14 +198,14 @@ int launch_tma(const uint8_t *msgs, uint32_t out_len, uint8_t *digests, uint64_t
     return cuda_status(cudaGetLastError());
 }
 
-// True when p is device memory of the current device (not host-mapped).
-bool device_resident(const void *p) {
+// True when p is device memory of this device (not host-mapped, not a peer's).
+bool device_resident(const void *p, int device) {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 template <int V>
@@ -222,7 +222,8 @@ int launch_variant(const uint8_t *msgs, uint64_t stride, uint64_t len, uint32_t 
             if (a8) return launch_one<V, -1, true, InterleavedRep>(msgs, stride, len, out_len, digests, n, stream, dev);
         }
     }
-    if (len == 64 && stride == 64 && a16 && tuning_get(KB_TUNE_STAGING) == KB_STAGING_TMA && device_resident(msgs))
+    if (len == 64 && stride == 64 && a16 && tuning_get(KB_TUNE_STAGING) == KB_STAGING_TMA &&
+        device_resident(msgs, dev.device))
         return launch_tma<V>(msgs, out_len, digests, n, stream, dev);
     if (len == 64 && a16) return launch_one<V, 64, true, PlainRep>(msgs, stride, len, out_len, digests, n, stream, dev);
     constexpr int rate = Variant<V>::rate;
