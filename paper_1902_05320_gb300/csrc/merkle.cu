@@ -414,9 +414,10 @@ int launch_merkle_many(const uint8_t *buf, uint64_t n_trees, uint64_t leaves_per
     // Leaves on 8-byte boundaries (buffer and leaf size) take the aligned
     // 8-byte loads; others the byte-exact reads.
     const bool a8 = ((reinterpret_cast<uintptr_t>(buf) | leaf_bytes) & 7) == 0;
-    const void *fn = a8 ? reinterpret_cast<const void *>(&k_merkle_many<true>)
-                        : reinterpret_cast<const void *>(&k_merkle_many<false>);
-    const uint64_t grid = persistent_grid(fn, kThreads, 0, n_trees, dev);
+    // One thread per tree and as many blocks as that takes: the block
+    // scheduler balances the last wave, where a grid-stride split would give
+    // some threads one tree more than others.
+    const uint64_t grid = std::min<uint64_t>((n_trees + kThreads - 1) / kThreads, uint64_t(INT32_MAX));
     if (a8)
         k_merkle_many<true><<<unsigned(grid), kThreads, 0, stream>>>(buf, n_trees, leaves_per_tree, leaf_bytes,
                                                                       roots);

@@ -13,6 +13,9 @@
 //   376         u64 total bytes absorbed
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
+
 #include "keccak_core.cuh"
 #include "runtime.cuh"
 #include "sponge.cuh"
@@ -137,7 +140,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     }
 }
 
-uint64_t grid_for(const void *fn, uint64_t n, const DeviceInfo &dev) { return persistent_grid(fn, kThreads, 0, n, dev); }
+// One thread per message and as many blocks as that takes (the block
+// scheduler balances the last wave; a grid-stride split would give some
+// threads one message more than others).
+uint64_t grid_for(const void *, uint64_t n, const DeviceInfo &) {
+    return std::min<uint64_t>((n + kThreads - 1) / kThreads, uint64_t(INT32_MAX));
+}
 
 }  // namespace
 

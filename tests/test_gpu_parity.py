@@ -99,6 +99,26 @@ def test_uniform_64_byte_staging(cuda_lib, oracle_mod, restore_tuning, n, varian
     assert cuda_lib.keccak_last_error() == 0
 
 
+@pytest.mark.parametrize("out_len", [0, 1, 31, 168, 169, 337])
+@pytest.mark.parametrize("staging", [0, 1])
+def test_uniform_64_byte_shake_output_lengths(cuda_lib, oracle_mod, restore_tuning, out_len, staging):
+    # SHAKE128 of 64-byte messages: empty, short, exactly one rate block and
+    # just past it, two blocks; loaded directly and staged by bulk copies.
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_STAGING, staging)
+    n = 300
+    msgs = W.uniform_messages(n, 64, seed=950 + out_len)
+    if out_len == 0:
+        torch = _torch()
+        buf = dev(msgs)
+        out = torch.full((16,), 0xEE, dtype=torch.uint8, device="cuda")
+        cuda_lib.keccak_batch_uniform(buf, 64, 64, 4, 0, out, n)
+        assert (host(out) == 0xEE).all()
+        return
+    got = gpu_uniform(cuda_lib, msgs, 64, 64, 4, out_len, n)
+    want = oracle_uniform(oracle_mod, msgs, 64, 64, 4, out_len, n)
+    assert np.array_equal(got, want)
+
+
 def test_uniform_zero_stride_and_single_message(cuda_lib, oracle_mod):
     msgs = W.random_bytes(300, seed=5)
     got = gpu_uniform(cuda_lib, msgs, 0, 300, 3, 64, 37)
