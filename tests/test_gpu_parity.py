@@ -305,6 +305,33 @@ def test_full_size_ragged_batch_sampled(cuda_lib, oracle_mod):
     assert cuda_lib.keccak_last_error() == 0
 
 
+def test_full_size_ragged_batch_every_digest_against_hashlib(cuda_lib):
+    # Beyond the oracle's sample: all 2^20 digests of the full-size mixed batch
+    # against Python's hashlib (OpenSSL), hashed on host threads.
+    import hashlib
+    from concurrent.futures import ThreadPoolExecutor
+
+    b = W.ragged_batch(1 << 20, seed=3, max_len=65536)
+    got = _run_ragged(cuda_lib, b)
+    fns = (hashlib.sha3_224, hashlib.sha3_256, hashlib.sha3_384, hashlib.sha3_512)
+
+    def part(lo, hi):
+        out = []
+        for i in range(lo, hi):
+            o, ln, v, d = int(b.offsets[i]), int(b.lens[i]), int(b.variants[i]), int(b.out_lens[i])
+            m = b.msgs[o:o + ln]
+            if v < 4:
+                out.append(fns[v](m).digest())
+            else:
+                out.append((hashlib.shake_128 if v == 4 else hashlib.shake_256)(m).digest(d))
+        return b"".join(out)
+
+    step = 8192
+    with ThreadPoolExecutor(THREADS) as ex:
+        parts = list(ex.map(lambda lo: part(lo, min(b.n, lo + step)), range(0, b.n, step)))
+    assert got.tobytes() == b"".join(parts)
+
+
 def test_full_size_merkle_root(cuda_lib, oracle_mod):
     torch = _torch()
     n, lb = 524288, 8192
