@@ -489,6 +489,24 @@ def _lanes_to_bits(lanes: np.ndarray, w: int) -> np.ndarray:
     return np.array([(int(lanes[i]) >> z) & 1 for i in range(25) for z in range(w)], dtype=np.uint8)
 
 
+@pytest.mark.parametrize("b,nr", [(200, 18), (1600, 24), (1600, 12)])
+def test_keccak_p_several_tiles(cuda_lib, oracle_mod, b, nr):
+    # 3 full tiles of 128 states and a partial one; the states after the n
+    # given ones stay untouched.
+    torch = _torch()
+    w = b // 25
+    n, extra = 128 * 3 + 77, 5
+    rng = np.random.default_rng(b + nr)
+    states = rng.integers(0, 2**64, size=(n + extra, 25), dtype=np.uint64) & np.uint64((1 << w) - 1)
+    d = torch.from_numpy(states.view(np.int64).copy()).cuda()
+    cuda_lib.keccak_p_batch(d, b, nr, n)
+    got = d.cpu().numpy().view(np.uint64).reshape(n + extra, 25)
+    assert np.array_equal(got[n:], states[n:])
+    for i in list(range(0, n, 37)) + [127, 128, 383, 384, n - 1]:
+        want = oracle_mod.keccak_p(b, nr, _lanes_to_bits(states[i], w))
+        assert np.array_equal(_lanes_to_bits(got[i], w), want), (b, nr, i)
+
+
 @pytest.mark.parametrize("b", [25, 50, 100, 200, 400, 800, 1600])
 def test_keccak_p_every_width_and_round_count(cuda_lib, oracle_mod, b):
     torch = _torch()
