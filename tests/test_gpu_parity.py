@@ -119,6 +119,20 @@ def test_uniform_64_byte_shake_output_lengths(cuda_lib, oracle_mod, restore_tuni
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("staging", [0, 1])
+def test_long_shake_outputs(cuda_lib, oracle_mod, restore_tuning, staging):
+    # Outputs of hundreds of squeeze blocks, fixed-stride and ragged.
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_STAGING, staging)
+    msgs = W.uniform_messages(5, 64, seed=990)
+    got = gpu_uniform(cuda_lib, msgs, 64, 64, 5, 70001, 5)
+    want = oracle_uniform(oracle_mod, msgs, 64, 64, 5, 70001, 5)
+    assert np.array_equal(got, want)
+    b = W.ragged_batch(3, seed=991, lens=np.array([0, 300, 5000]), gap=3)
+    b.variants = np.array([4, 5, 1], dtype=np.uint8)
+    b.out_lens = np.array([100003, 1, 32], dtype=np.uint32)
+    assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
+
+
 def test_uniform_zero_stride_and_single_message(cuda_lib, oracle_mod):
     msgs = W.random_bytes(300, seed=5)
     got = gpu_uniform(cuda_lib, msgs, 0, 300, 3, 64, 37)
