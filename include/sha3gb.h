@@ -63,9 +63,9 @@ typedef enum {
 #define KB_DEV_TIMEOUT 0x4u       /* a bounded device wait expired */
 
 /*
- * keccak_batch_uniform -- the fixed-stride batch mode (Section 4, "Batch mode
- * ... divide a piece of information into multiple identical slices"; Section
- * 4.3 hashes many same-length messages): message i is the `len` bytes at
+ * keccak_batch_uniform -- the fixed-stride batch mode (Section 4: the input
+ * split into equal parts that are hashed independently; Section 4.3 hashes
+ * many same-length messages): message i is the `len` bytes at
  * msgs + i*stride, i = 0..n-1, all hashed with one variant.  Output i is
  * `out_len` bytes at digests + i*out_len.
  *   msgs     device, >= (n-1)*stride + len bytes (may be NULL when len == 0)
@@ -191,10 +191,11 @@ int keccak_stream_absorb(uint8_t *states, const uint8_t *msgs, const uint64_t *o
 int keccak_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *digests, uint64_t n, void *stream);
 
 /*
- * merkle_sha3_256 -- tree mode (Section 4: messages "hashed in twos until the
- * Hash Root").  The buffer holds n_leaves leaves of leaf_bytes bytes each;
- * leaf digest = SHA3-256(0x00 || leaf), node digest = SHA3-256(0x01 || left
- * || right), level by level, an odd last node carried up unchanged.
+ * merkle_sha3_256 -- tree mode (Section 4: digests combined pairwise, level
+ * after level, up to a single root).  The buffer holds n_leaves leaves of
+ * leaf_bytes bytes each; leaf digest = SHA3-256(0x00 || leaf), node digest =
+ * SHA3-256(0x01 || left || right), level by level, an odd last node carried
+ * up unchanged.
  *   buf        device, n_leaves*leaf_bytes bytes
  *   root       HOST, 32 bytes, written before the call returns
  * Synchronous on `stream`.  n_leaves == 0 or leaf_bytes == 0 is
@@ -206,7 +207,7 @@ int merkle_sha3_256(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, 
 
 /*
  * merkle_sha3_256_many -- many small trees at once, one thread per tree: the
- * "one thread one tree" granularity Section 4.1 names for tree mode.  Tree t
+ * granularity Section 4.1 gives for tree mode, a thread per tree.  Tree t
  * is leaves t*leaves_per_tree .. (t+1)*leaves_per_tree - 1 of buf (leaf_bytes
  * bytes each), with the leaf/node rules of merkle_sha3_256; its root goes to
  * roots + 32*t.

@@ -335,7 +335,7 @@ int oracle_inc_final(oracle_inc *st, uint8_t *out, size_t out_len) {
 }
 
 /* ---------------------------------------------------------------------------
- * Tree mode (Section 4: messages "hashed in twos until the Hash Root").  The
+ * Tree mode (Section 4: digests combined pairwise up to one root).  The
  * paper fixes no node format; the library's rules are: leaf digest
  * SHA3-256(0x00 || leaf), node digest SHA3-256(0x01 || left || right), one
  * level at a time, an odd last node carried up unchanged.

@@ -1,5 +1,6 @@
-// merkle.cu -- tree mode (Section 4: messages "hashed in twos until the Hash
-// Root", named there as future work done with reductions).
+// merkle.cu -- tree mode (Section 4: digests combined pairwise, level after
+// level, up to one root; the paper leaves it to future work with
+// reductions).
 //
 // Node format: leaf = SHA3-256(0x00 || leaf bytes), inner node =
 // SHA3-256(0x01 || left || right); levels are reduced one at a time and an odd

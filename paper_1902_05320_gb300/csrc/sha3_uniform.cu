@@ -1,5 +1,5 @@
 // sha3_uniform.cu -- fixed-stride batch kernel: one thread per message
-// (the paper's "one thread per message" granularity, Section 4.1), every
+// (the paper's granularity of a thread per message, Section 4.1), every
 // message the same length and variant (Section 4.3).
 //
 // Specialisations: for each variant, a compile-time 64-byte message read with

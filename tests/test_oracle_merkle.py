@@ -1,6 +1,6 @@
 """Pins the oracle's tree mode against a second, recursive definition.
 
-The paper's tree mode (Section 4) hashes messages "in twos" up to a root and
+The paper's tree mode (Section 4) combines digests pairwise up to a root and
 fixes no node format; the library's rules are leaf = SHA3-256(0x00 || leaf),
 node = SHA3-256(0x01 || left || right), one level at a time, an odd last node
 carried up unchanged.  Level-by-level pairing with that carry equals the
