@@ -692,13 +692,20 @@ def measured_traffic():
 
 
 def csrc_digest() -> str:
+    """Hash of the headline kernel's sources with comments and blank space
+    removed, so that only changes to the code itself invalidate the profile."""
+    import re
+
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1902_05320_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if name in ("keccak_core.cuh", "keccak_interleaved.cuh", "sponge.cuh", "sha3_uniform.cu", "runtime.cuh",
                     "tma.cuh"):
+            text = open(os.path.join(csrc, name), encoding="utf-8").read()
+            text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", " ", text)
             h.update(name.encode())
-            h.update(open(os.path.join(csrc, name), "rb").read())
+            h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
