@@ -343,7 +343,18 @@ def test_full_size_ragged_batch_every_digest_against_hashlib(cuda_lib):
     step = 8192
     with ThreadPoolExecutor(THREADS) as ex:
         parts = list(ex.map(lambda lo: part(lo, min(b.n, lo + step)), range(0, b.n, step)))
-    assert got.tobytes() == b"".join(parts)
+    want = b"".join(parts)
+    assert got.tobytes() == want
+    # The configuration the autotuner picks for this batch, as the bench runs it.
+    torch = _torch()
+    d = [dev(x) for x in (b.msgs, b.offsets, b.lens, b.variants, b.out_lens)]
+    out = torch.full((b.total_out(),), 0xEE, dtype=torch.uint8, device="cuda")
+    cuda_lib.keccak_batch_autotune(*d, out, b.n)
+    out.fill_(0xEE)
+    cuda_lib.keccak_batch(*d, out, b.n)
+    assert host(out).tobytes() == want
+    torch.cuda.synchronize()
+    cuda_lib.keccak_release()  # drops the tuned configuration with the cached scratch
 
 
 def test_full_size_merkle_root(cuda_lib, oracle_mod):
