@@ -1,7 +1,8 @@
 """The serving loop (kb_server_*): continuous batching of requests that arrive
-one by one, admitted against a device-memory budget.  Every output is checked
-against the CPU oracle, and each result must be the same when the message is
-hashed alone as when it went through the server mixed with others."""
+one by one, admitted against a device-memory budget.  Outputs are checked
+against the CPU oracle (all of them at small loads, a sample at the full
+bench load), and each result must be the same when the message is hashed
+alone as when it went through the server mixed with others."""
 import os
 
 import numpy as np
@@ -106,3 +107,39 @@ def test_server_submit_and_wait(cuda_lib, oracle_mod):
         for (t, variant, out_len), o, m in zip(tickets, outs, msgs):
             srv.wait(t, timeout_ms=20_000)
             assert o.numpy()[:out_len].tobytes() == oracle_mod.hash(variant, m.tobytes(), out_len)
+
+
+def test_full_size_serving_run_sampled(cuda_lib, oracle_mod):
+    # The bench's serving load in full (Poisson 200k req/s for 10 s, 32 B..1 MiB,
+    # a 4 GiB pool, a 2 GiB budget): every request completes, 300 sampled
+    # outputs equal the oracle's and 20,000 equal hashlib's.
+    import hashlib
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    from paper_1902_05320_gb300.serve import Server
+
+    wl = W.serving_workload(200_000, 10.0, seed=5, pool_bytes=4 << 30)
+    with Server(hbm_budget_bytes=2 << 30, max_inflight=16, max_batch_requests=4096) as srv:
+        got, lat, stats, _ = _replay(srv, torch, wl)
+    assert stats["requests"] == wl.n and (lat > 0).all()
+    pos = np.concatenate([[0], np.cumsum(wl.out_lens[:-1], dtype=np.uint64)])
+    rng = np.random.default_rng(55)
+    idx = rng.choice(wl.n, size=300, replace=False)
+    want = oracle_mod.hash_batch(wl.pool, wl.offsets[idx], wl.lens[idx], wl.variants[idx], wl.out_lens[idx], THREADS)
+    at = 0
+    for i in idx:
+        ln = int(wl.out_lens[i])
+        assert np.array_equal(got[int(pos[i]):int(pos[i]) + ln], want[at:at + ln]), i
+        at += ln
+    fns = (hashlib.sha3_224, hashlib.sha3_256, hashlib.sha3_384, hashlib.sha3_512)
+
+    def check(i):
+        o, ln, v, d = int(wl.offsets[i]), int(wl.lens[i]), int(wl.variants[i]), int(wl.out_lens[i])
+        m = wl.pool[o:o + ln]
+        h = fns[v](m).digest() if v < 4 else (hashlib.shake_128 if v == 4 else hashlib.shake_256)(m).digest(d)
+        return h == got[int(pos[i]):int(pos[i]) + d].tobytes()
+
+    with ThreadPoolExecutor(THREADS) as ex:
+        assert all(ex.map(check, rng.choice(wl.n, size=20_000, replace=False)))
