@@ -249,6 +249,9 @@ def main() -> None:
                     help="only run the ragged-batch measurement on N messages (profiling captures)")
     ap.add_argument("--next-only", action="store_true",
                     help="only run the streaming, many-tree, message-tree and Keccak-p measurements")
+    ap.add_argument("--config", type=int, default=0, choices=sorted(CONFIG_WORKLOADS),
+                    help="only run the measurement of one workload: " +
+                         "; ".join(f"{k}: {v}" for k, v in CONFIG_WORKLOADS.items()))
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -279,6 +282,9 @@ def main() -> None:
     if args.ragged_only:
         print(json.dumps(ragged_measurements(binding, workloads, torch, torch.cuda.current_stream(), rank,
                                              n=args.ragged_only, autotune=False)), flush=True)
+        return
+    if args.config:
+        print(json.dumps(config_measurement(args.config, binding, workloads, torch, rank)), flush=True)
         return
     if args.next_only:
         print(json.dumps(next_rows_measurements(binding, workloads, torch, torch.cuda.current_stream(), rank)),
@@ -394,7 +400,25 @@ def main() -> None:
 
 
 def extra_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
-    """Secondary figures of the same fixed-length batch family (not the headline)."""
+    """Secondary figures: the rest of the fixed-length family, then the other
+    workloads (not the headline)."""
+    out = fixed_length_measurements(binding, workloads, torch, stream, msgs, rank)
+    out["small_batches"] = small_batch_measurements(binding, workloads, torch, stream, rank)
+    out["ragged_2p20_loguniform_0_64KiB"] = ragged_measurements(binding, workloads, torch, stream, rank)
+    out["serving_poisson_200k_rps_10s"] = serving_measurements(workloads, torch, rank)
+    out["merkle_4GiB_8KiB_leaves"] = merkle_measurements(binding, workloads, torch, stream, rank)
+    out["next_rows"] = next_rows_measurements(binding, workloads, torch, stream, rank)
+    try:
+        out["int_lanes_per_sm_clk"] = {name: round(binding.int_issue_probe(op, 4096, stream), 2)
+                                       for op, name in enumerate(("lop3", "shf", "prmt", "iadd"))}
+    except Exception as e:  # diagnostic only
+        out["int_lanes_per_sm_clk"] = f"probe failed: {e}"
+    return out
+
+
+def fixed_length_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
+    """2^24 x 64 B with the two state-layout and staging controls and with
+    SHA3-512, and 2^22 x 1 KiB SHA3-256."""
     out = {}
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -437,17 +461,45 @@ def extra_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
     out["sha3_256_2p22_x_1KiB_mhash_s"] = n2 / ms / 1e3
     out["sha3_256_2p22_x_1KiB_gb_s"] = n2 * l2 / ms / 1e6
     del m2, d2
-    out["small_batches"] = small_batch_measurements(binding, workloads, torch, stream, rank)
-    out["ragged_2p20_loguniform_0_64KiB"] = ragged_measurements(binding, workloads, torch, stream, rank)
-    out["serving_poisson_200k_rps_10s"] = serving_measurements(workloads, torch, rank)
-    out["merkle_4GiB_8KiB_leaves"] = merkle_measurements(binding, workloads, torch, stream, rank)
-    out["next_rows"] = next_rows_measurements(binding, workloads, torch, stream, rank)
-    try:
-        out["int_lanes_per_sm_clk"] = {name: round(binding.int_issue_probe(op, 4096, stream), 2)
-                                       for op, name in enumerate(("lop3", "shf", "prmt", "iadd"))}
-    except Exception as e:  # diagnostic only
-        out["int_lanes_per_sm_clk"] = f"probe failed: {e}"
     return out
+
+
+CONFIG_WORKLOADS = {
+    1: "4096 x 64 B SHA3-256, one launch (and 119,040 x 10 B, the paper's largest batch)",
+    2: "2^24 x 64 B SHA3-256 and SHA3-512, 2^22 x 1 KiB SHA3-256",
+    3: "2^20 ragged messages, lengths log-uniform 0..64 KiB, six functions mixed",
+    4: "Merkle root of 4 GiB in 8 KiB leaves",
+    5: "serving: Poisson arrivals at 200k requests/s for 10 s, 32 B..1 MiB, 2 GiB HBM budget",
+}
+
+
+def config_measurement(config, binding, workloads, torch, rank) -> dict:
+    """One workload's measurement on its own (bench.py --config N)."""
+    stream = torch.cuda.current_stream()
+    if config == 1:
+        res = small_batch_measurements(binding, workloads, torch, stream, rank)
+    elif config == 2:
+        msgs = torch.from_numpy(workloads.uniform_messages(N_MSGS, MSG_BYTES, seed=rank_seed(1, rank))).cuda()
+        d = torch.empty(N_MSGS * DIGEST, dtype=torch.uint8, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            binding.keccak_batch_uniform(msgs, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, d, N_MSGS, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(10):
+            binding.keccak_batch_uniform(msgs, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, d, N_MSGS, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        del d
+        res = {"sha3_256_2p24_x_64B_mhash_s": N_MSGS / (e0.elapsed_time(e1) / 10) / 1e3}
+        res.update(fixed_length_measurements(binding, workloads, torch, stream, msgs, rank))
+    elif config == 3:
+        res = ragged_measurements(binding, workloads, torch, stream, rank)
+    elif config == 4:
+        res = merkle_measurements(binding, workloads, torch, stream, rank)
+    else:
+        res = serving_measurements(workloads, torch, rank)
+    return {"config": config, "workload": CONFIG_WORKLOADS[config], "result": res}
 
 
 RATES = (144, 136, 104, 72, 168, 136)

@@ -116,10 +116,32 @@ int keccak_batch(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *l
  * Synchronous.  The chosen register budget, blocks per SM and its time in ms
  * are written to the HOST pointers when they are not NULL.  Allocates a
  * temporary device copy of the outputs.
+ * Environment, read by the library:
+ *   SHA3GB_TUNE_CACHE  a file path: configurations the autotuner finds are
+ *     written there and read back by later processes on the same kind of GPU.
+ *     JSON Lines, one object per GPU name, SM count and size class
+ *     floor(log2 n): {"gpu": "...", "sms": S, "size_class": C,
+ *     "min_blocks": M, "blocks_per_sm": B}.  Unreadable files and lines that
+ *     do not parse are ignored.
+ *   SHA3GB_TUNE  "off": keccak_batch ignores tuned configurations; "full":
+ *     keccak_batch tunes a size class the first time it sees it (that call
+ *     is then synchronous and allocates as keccak_batch_autotune does, and
+ *     not inside stream capture); "cached" or unset: configurations found by
+ *     keccak_batch_autotune or read from the file are used.
  */
 int keccak_batch_autotune(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
                           const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
                           void *stream, int64_t *chosen_min_blocks, int64_t *chosen_blocks_per_sm, float *ms);
+
+/*
+ * keccak_tuned_config -- the configuration keccak_batch's queue schedule
+ * would use for a batch of n messages on the current device, after the
+ * tuning knobs, the tuned configurations and the cache file: the register
+ * budget (blocks per SM the kernel is compiled for) and the blocks per SM of
+ * the launch (0: as many as fit), written to the HOST pointers when not NULL.
+ * Returns KB_OK, or KB_ERR_CUDA when no device can be used.
+ */
+int keccak_tuned_config(uint64_t n, int64_t *min_blocks, int64_t *blocks_per_sm);
 
 /*
  * keccak_batch_noalloc -- keccak_batch for callers that cannot allocate

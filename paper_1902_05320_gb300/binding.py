@@ -53,6 +53,7 @@ _SIGS = {
                                                                       ctypes.c_void_p, ctypes.c_void_p,
                                                                       ctypes.c_void_p]),
     "keccak_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_uint64, ctypes.c_void_p]),
+    "keccak_tuned_config": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "keccak_batch_uniform_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                                  ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
                                                  ctypes.c_void_p]),
@@ -146,6 +147,14 @@ def keccak_batch_autotune(msgs, offsets, lens, variants, out_lens, digests, n: i
                                         _ptr(digests), n, _stream(stream), ctypes.addressof(minb),
                                         ctypes.addressof(bps), ctypes.addressof(ms)), "keccak_batch_autotune")
     return {"min_blocks": minb.value, "blocks_per_sm": bps.value, "ms": ms.value}
+
+
+def keccak_tuned_config(n: int) -> dict:
+    """The register budget and blocks per SM keccak_batch's queue schedule
+    would use for n messages on the current device."""
+    minb, bps = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().keccak_tuned_config(n, ctypes.addressof(minb), ctypes.addressof(bps)), "keccak_tuned_config")
+    return {"min_blocks": minb.value, "blocks_per_sm": bps.value}
 
 
 def keccak_batch_noalloc(msgs, offsets, lens, variants, out_lens, digests, n: int, stream=None) -> None:

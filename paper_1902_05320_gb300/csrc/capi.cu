@@ -146,6 +146,14 @@ int keccak_batch_autotune(const uint8_t *msgs, const uint64_t *offsets, const ui
                                  ms);
 }
 
+int keccak_tuned_config(uint64_t n, int64_t *min_blocks, int64_t *blocks_per_sm) {
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    queue_config_for(n, *dev, min_blocks, blocks_per_sm);
+    return KB_OK;
+}
+
 uint64_t merkle_node_count(uint64_t n_leaves) { return merkle_nodes(n_leaves); }
 
 int merkle_sha3_256_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes,

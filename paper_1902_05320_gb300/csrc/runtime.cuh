@@ -89,6 +89,9 @@ int autotune_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const ui
                           const DeviceInfo &dev, int64_t *best_minb, int64_t *best_bps, float *best_ms);
 void release_queue_graphs(int device);
 void forget_tuning(int device);
+// The register budget and blocks per SM keccak_batch's queue schedule would
+// use for n messages on this device (0 blocks per SM: as many as fit).
+void queue_config_for(uint64_t n, const DeviceInfo &dev, int64_t *min_blocks, int64_t *blocks_per_sm);
 uint64_t merkle_nodes(uint64_t n_leaves);
 int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes,
                          cudaStream_t stream, const DeviceInfo &dev);

@@ -21,10 +21,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <list>
 #include <mutex>
+#include <set>
+#include <string>
 #include <tuple>
+#include <vector>
 
 #include "keccak_core.cuh"
 #include "lane_parallel.cuh"
@@ -364,12 +369,136 @@ std::list<TuneEntry> g_tuned;
 
 int size_class(uint64_t n) { return n ? 63 - __builtin_clzll(n) : 0; }
 
+// ---- the tuned configurations kept in a file (SHA3GB_TUNE_CACHE) ---------------
+//
+// When SHA3GB_TUNE_CACHE names a file, configurations found by the autotuner
+// are written there and read back by later processes.  The file holds JSON
+// Lines, one object per entry in the fixed form this file writes:
+//   {"gpu": NAME, "sms": SMs, "size_class": floor(log2 n),
+//    "min_blocks": register budget (blocks per SM compiled for),
+//    "blocks_per_sm": blocks per SM of the launch}
+// Entries are matched on the GPU's name and SM count; lines that do not
+// parse are ignored, and I/O failures leave the in-memory tuning as it is.
+
+struct CacheLine {
+    std::string gpu;
+    int sms = 0, size_class = 0, minb = 0, bps = 0;
+};
+
+const char *cache_path() {
+    const char *p = std::getenv("SHA3GB_TUNE_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+
+std::string gpu_name(int device) {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::string name = prop.name;
+    for (char &ch : name)  // kept out of the JSON string: quotes, backslashes, controls
+        if (ch == '"' || ch == '\\' || static_cast<unsigned char>(ch) < 0x20) ch = '_';
+    return name;
+}
+
+constexpr const char *kCacheFormat =
+    "{\"gpu\": \"%s\", \"sms\": %d, \"size_class\": %d, \"min_blocks\": %d, \"blocks_per_sm\": %d}\n";
+
+bool valid_minb(int m) { return m == 2 || m == 3 || m == 4 || m == 5 || m == 6 || m == 8; }
+
+std::vector<CacheLine> read_cache(const char *path) {
+    std::vector<CacheLine> out;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return out;
+    char buf[512];
+    while (std::fgets(buf, sizeof buf, f)) {
+        CacheLine c;
+        char name[256];
+        if (std::sscanf(buf, "{\"gpu\": \"%255[^\"]\", \"sms\": %d, \"size_class\": %d, \"min_blocks\": %d, "
+                             "\"blocks_per_sm\": %d}",
+                        name, &c.sms, &c.size_class, &c.minb, &c.bps) != 5)
+            continue;
+        c.gpu = name;
+        if (c.size_class < 0 || c.size_class > 63 || !valid_minb(c.minb) || c.bps < 0 || c.bps > 32) continue;
+        out.push_back(c);
+    }
+    std::fclose(f);
+    return out;
+}
+
+std::set<int> g_cache_loaded;  // devices whose file entries are in g_tuned (under g_tune_mu)
+
+// Adds this GPU's entries of the file to g_tuned, once per device.
+void load_cache_locked(const DeviceInfo &dev) {
+    if (g_cache_loaded.count(dev.device)) return;
+    g_cache_loaded.insert(dev.device);
+    const char *path = cache_path();
+    if (!path) return;
+    const std::string name = gpu_name(dev.device);
+    for (const CacheLine &c : read_cache(path)) {
+        if (c.gpu != name || c.sms != dev.sm_count) continue;
+        bool have = false;
+        for (const auto &t : g_tuned) have = have || (t.device == dev.device && t.size_class == c.size_class);
+        if (have) continue;
+        QueueConfig cfg;
+        cfg.minb = c.minb;
+        cfg.blocks_per_sm = c.bps;
+        g_tuned.push_back(TuneEntry{dev.device, c.size_class, cfg});
+    }
+}
+
+// Writes one entry to the file, replacing an older one with the same key.
+void save_cache_entry(const DeviceInfo &dev, int sc, const QueueConfig &cfg) {
+    const char *path = cache_path();
+    if (!path) return;
+    const std::string name = gpu_name(dev.device);
+    std::vector<CacheLine> lines = read_cache(path);
+    lines.erase(std::remove_if(lines.begin(), lines.end(),
+                               [&](const CacheLine &c) {
+                                   return c.gpu == name && c.sms == dev.sm_count && c.size_class == sc;
+                               }),
+                lines.end());
+    lines.push_back(CacheLine{name, dev.sm_count, sc, cfg.minb, cfg.blocks_per_sm});
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const CacheLine &c : lines)
+        std::fprintf(f, kCacheFormat, c.gpu.c_str(), c.sms, c.size_class, c.minb, c.bps);
+    if (std::fclose(f) == 0) std::rename(tmp.c_str(), path);
+}
+
+// SHA3GB_TUNE: "off" ignores tuned configurations, "full" tunes a batch's
+// size class on first sight inside keccak_batch, anything else (or unset)
+// uses the configurations keccak_batch_autotune found ("cached").
+enum class TuneMode { Cached, Off, Full };
+TuneMode tune_mode() {
+    static const TuneMode mode = [] {
+        const char *m = std::getenv("SHA3GB_TUNE");
+        if (m && std::strcmp(m, "off") == 0) return TuneMode::Off;
+        if (m && std::strcmp(m, "full") == 0) return TuneMode::Full;
+        return TuneMode::Cached;
+    }();
+    return mode;
+}
+
+bool use_tuned() { return tuning_get(KB_TUNE_AUTOTUNE) != 0 && tune_mode() != TuneMode::Off; }
+
+bool have_tuned(uint64_t n, const DeviceInfo &dev) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_cache_locked(dev);
+    for (const auto &t : g_tuned)
+        if (t.device == dev.device && t.size_class == size_class(n)) return true;
+    return false;
+}
+
 QueueConfig choose_config(uint64_t n, const DeviceInfo &dev) {
     QueueConfig cfg;
     const int64_t regs = tuning_get(KB_TUNE_QUEUE_MIN_BLOCKS);
     const int64_t bps = tuning_get(KB_TUNE_QUEUE_BLOCKS_PER_SM);
-    if (tuning_get(KB_TUNE_AUTOTUNE) != 0) {
+    if (use_tuned()) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        load_cache_locked(dev);
         for (const auto &t : g_tuned)
             if (t.device == dev.device && t.size_class == size_class(n)) {
                 cfg = t.cfg;
@@ -395,6 +524,15 @@ int launch_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const uint
                         const DeviceInfo &dev) {
     const uint64_t ntiles = digest_offsets_tiles(n);
     int err = KB_OK;
+    // SHA3GB_TUNE=full: a size class seen for the first time is tuned here
+    // (synchronously), which also leaves this batch's digests.
+    cudaStreamCaptureStatus cap0 = cudaStreamCaptureStatusNone;
+    if (tune_mode() == TuneMode::Full && use_tuned() && tuning_get(KB_TUNE_RAGGED_SCHEDULE) == KB_SCHEDULE_QUEUE &&
+        tuning_get(KB_TUNE_QUEUE_MIN_BLOCKS) == 0 && tuning_get(KB_TUNE_QUEUE_BLOCKS_PER_SM) == 0 &&
+        cudaStreamIsCapturing(stream, &cap0) == cudaSuccess && cap0 == cudaStreamCaptureStatusNone &&
+        !have_tuned(n, dev))
+        return autotune_ragged_queue(msgs, offsets, lens, variants, out_lens, digests, n, stream, dev, nullptr,
+                                     nullptr, nullptr);
     const size_t bytes = scratch_bytes(n, ntiles);
     uint8_t *scratch = static_cast<uint8_t *>(stream_scratch(stream, bytes, &err));
     if (!scratch) return err;
@@ -548,9 +686,11 @@ int autotune_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const ui
     if (rc != KB_OK) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        load_cache_locked(dev);
         for (auto it = g_tuned.begin(); it != g_tuned.end();)
             it = (it->device == dev.device && it->size_class == size_class(n)) ? g_tuned.erase(it) : std::next(it);
         g_tuned.push_front(TuneEntry{dev.device, size_class(n), best});
+        save_cache_entry(dev, size_class(n), best);
     }
     // Leave the caller's digests from the chosen configuration.
     rc = issue(msgs, offsets, lens, variants, out_lens, digests, n, bf, ntiles, best, queue_grid(best, n, dev), stream,
@@ -565,6 +705,14 @@ void forget_tuning(int device) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto it = g_tuned.begin(); it != g_tuned.end();)
         it = (device < 0 || it->device == device) ? g_tuned.erase(it) : std::next(it);
+    if (device < 0) g_cache_loaded.clear();
+    else g_cache_loaded.erase(device);
+}
+
+void queue_config_for(uint64_t n, const DeviceInfo &dev, int64_t *min_blocks, int64_t *blocks_per_sm) {
+    const QueueConfig cfg = choose_config(n, dev);
+    if (min_blocks) *min_blocks = cfg.minb;
+    if (blocks_per_sm) *blocks_per_sm = cfg.blocks_per_sm;
 }
 
 }  // namespace kb
