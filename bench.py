@@ -316,17 +316,20 @@ def main() -> None:
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # One event between consecutive steps: the first and last bracket the
+    # whole timed region, the others give each step's own time.
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     sampler.mark()
-    start.record(stream)
-    for _ in range(args.steps):
+    marks[0].record(stream)
+    for k in range(args.steps):
         step()
-    end.record(stream)
+        marks[k + 1].record(stream)
     torch.cuda.synchronize()
     sampler.mark()
     if world > 1:
         dist.barrier()
-    ms = start.elapsed_time(end) / args.steps
+    ms = marks[0].elapsed_time(marks[-1]) / args.steps
+    per_step = sorted(marks[k].elapsed_time(marks[k + 1]) for k in range(args.steps))
     time.sleep(0.2)
     sampler.stop()
     ms = max_over_ranks(ms, world)
@@ -372,7 +375,9 @@ def main() -> None:
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mhash/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms,
+        "ms_per_step_best": per_step[0], "ms_per_step_median": per_step[len(per_step) // 2],
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD if n_msgs == N_MSGS else f"sha3_256_{n_msgs}_msgs_x_64B",
                    "messages_per_gpu": n_msgs, "msg_bytes": MSG_BYTES,
