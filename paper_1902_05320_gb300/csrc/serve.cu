@@ -30,7 +30,7 @@
 #include <thread>
 #include <vector>
 
-#include "arena_ring.h"
+#include "arena_heap.h"
 #include "keccak_core.cuh"
 #include "lane_parallel.cuh"
 #include "runtime.cuh"
@@ -172,7 +172,7 @@ uint64_t request_cost(uint64_t len, int v, uint32_t out_len) {
 struct Lane {
     std::deque<uint32_t> pending;
     std::vector<Slot> slots;
-    ArenaRing ring;         // offsets relative to `base`
+    ArenaHeap heap;         // offsets relative to `base`
     uint64_t base = 0;      // start of this lane's part of the device arena
     uint64_t max_len = 0;   // longest message the lane can hold
 };
@@ -190,7 +190,7 @@ struct Server {
     uint64_t long_threshold = 64;     // cost (permutations) above which a request is long
     bool long_lanes_kernel = true;    // long lane: one warp per request
     Lane lanes[2];
-    std::mutex mu;                    // pending queues, slots, arena rings, stats
+    std::mutex mu;                    // pending queues, slots, arena heaps, stats
     std::condition_variable cv;
     std::unique_ptr<Request[]> chunks[kMaxChunks];
     std::atomic<uint32_t> n_requests{0};
@@ -256,7 +256,7 @@ struct Server {
         uint64_t start = 0;
         // Admission: the whole batch must fit in the free part of the budget;
         // otherwise shrink it (the oldest requests stay first in line).
-        while (!s.ids.empty() && !ln.ring.alloc(std::max<uint64_t>(bytes, 16), &start)) {
+        while (!s.ids.empty() && !ln.heap.alloc(std::max<uint64_t>(bytes, 16), &start)) {
             bytes -= align16(req(s.ids.back()).len);
             s.ids.pop_back();
         }
@@ -380,7 +380,7 @@ struct Server {
                         if (!ring_mode) complete(id, t);
                         bytes_done += req(id).len;
                     }
-                    ln.ring.free(s.region_start - ln.base);
+                    ln.heap.free(s.region_start - ln.base);
                     s.busy = false;
                     progress = true;
                 }
@@ -449,10 +449,10 @@ kb_server *kb_server_create(const kb_server_config *cfg, int *status) {
         s->long_threshold = cfg->long_threshold_perms ? cfg->long_threshold_perms : 64;
         s->long_lanes_kernel = cfg->long_lane_kernel != KB_SERVER_LONG_THREAD_PER_REQUEST;
         s->lanes[kShortLane].base = 0;
-        s->lanes[kShortLane].ring.reset(short_bytes);
+        s->lanes[kShortLane].heap.reset(short_bytes);
         s->lanes[kShortLane].max_len = short_bytes;
         s->lanes[kLongLane].base = short_bytes;
-        s->lanes[kLongLane].ring.reset(total - short_bytes);
+        s->lanes[kLongLane].heap.reset(total - short_bytes);
         s->lanes[kLongLane].max_len = total - short_bytes;
         if (cudaHostAlloc(&s->ring, sizeof(CompletionRing), cudaHostAllocMapped) != cudaSuccess) {
             cudaGetLastError();
@@ -597,7 +597,7 @@ int kb_server_replay(kb_server *handle, const uint8_t *pool, const uint64_t *off
         std::lock_guard<std::mutex> lk(s->mu);
         stats->batches = s->batches;
         stats->max_batch_requests_seen = s->max_batch_seen;
-        stats->peak_arena_bytes = s->lanes[0].ring.peak() + s->lanes[1].ring.peak();
+        stats->peak_arena_bytes = s->lanes[0].heap.peak() + s->lanes[1].heap.peak();
         stats->rejected = s->rejected;
         stats->completion_ring = s->ring_mode ? 1 : 0;
     }
