@@ -193,8 +193,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
 // The top of the tree, from a level of at most kTopCount nodes up to the
 // root, in one block: a block barrier separates the levels (each level is
 // written to global memory, which the barrier makes visible to the block).
-constexpr int kTopThreads = 512;
-constexpr uint64_t kTopCount = 4096;
+// Levels above that take one launch each over all SMs.  One SM hashes a
+// level of P parents in about P x 68 cycles once P fills it, so the block
+// starts only where a level is a single permutation's latency anyway (at
+// most 32 parents): from 4096 nodes it took ~165 us, where per-level launches
+// down to 64 nodes and the block from there take ~70 us.
+constexpr int kTopThreads = 64;
+constexpr uint64_t kTopCount = 64;
 
 __global__ void __launch_bounds__(kTopThreads) k_merkle_top(uint8_t *level, uint64_t count) {
     while (count > 1) {
