@@ -31,6 +31,8 @@
 #include <tuple>
 #include <vector>
 
+#include <unistd.h>
+
 #include "keccak_core.cuh"
 #include "lane_parallel.cuh"
 #include "runtime.cuh"
@@ -460,7 +462,9 @@ void save_cache_entry(const DeviceInfo &dev, int sc, const QueueConfig &cfg) {
                                }),
                 lines.end());
     lines.push_back(CacheLine{name, dev.sm_count, sc, cfg.minb, cfg.blocks_per_sm});
-    const std::string tmp = std::string(path) + ".tmp";
+    // A name of this process's own, so that processes saving at once do not
+    // write into each other's file; the last rename wins.
+    const std::string tmp = std::string(path) + ".tmp." + std::to_string(static_cast<long>(getpid()));
     FILE *f = std::fopen(tmp.c_str(), "w");
     if (!f) return;
     for (const CacheLine &c : lines)
