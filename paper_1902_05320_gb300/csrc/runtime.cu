@@ -4,6 +4,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <unordered_map>
 #include <utility>
 
@@ -20,7 +21,7 @@ struct Arena {
 struct DeviceSlot {
     DeviceInfo info;
     std::map<cudaStream_t, Arena> arenas;
-    std::unordered_map<const void *, int> occupancy;  // blocks/SM per (kernel, threads)
+    std::map<std::tuple<const void *, int, size_t>, int> occupancy;  // blocks/SM per (kernel, threads, smem)
 };
 
 std::mutex g_mu;
@@ -136,24 +137,25 @@ int tuning_set(int key, int64_t value) {
     return KB_OK;
 }
 
+// Resident blocks of `threads` per SM for kernel `fn` (occupancy API, cached).
+static int blocks_per_sm(const void *fn, int threads, size_t smem, const DeviceInfo &dev) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto &slot = g_devices[dev.device];
+    const auto key = std::make_tuple(fn, threads, smem);
+    auto it = slot.occupancy.find(key);
+    if (it != slot.occupancy.end()) return it->second;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    slot.occupancy[key] = per_sm;
+    return per_sm;
+}
+
 uint64_t persistent_grid(const void *fn, int threads, size_t smem, uint64_t work_items,
                          const DeviceInfo &dev) {
-    int per_sm = 0;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        auto &slot = g_devices[dev.device];
-        auto it = slot.occupancy.find(fn);
-        if (it != slot.occupancy.end()) {
-            per_sm = it->second;
-        } else {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
-                per_sm < 1) {
-                cudaGetLastError();
-                per_sm = 1;
-            }
-            slot.occupancy[fn] = per_sm;
-        }
-    }
+    const int per_sm = blocks_per_sm(fn, threads, smem, dev);
     const uint64_t full = uint64_t(per_sm) * uint64_t(dev.sm_count);
     const uint64_t need = (work_items + threads - 1) / threads;
     uint64_t g = need < full ? need : full;

@@ -133,6 +133,19 @@ def test_long_shake_outputs(cuda_lib, oracle_mod, restore_tuning, staging):
     assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
 
 
+@pytest.mark.parametrize("n,length,variant", [(119040, 10, 1), (121601, 10, 1), (250000, 10, 1), (60000, 100, 5),
+                                              (33, 7, 3)])
+def test_uniform_one_block_batches_around_one_wave(cuda_lib, oracle_mod, n, length, variant):
+    # One-block messages: a batch that one wave of single-warp blocks holds
+    # runs as that wave (119,040 is the paper's largest batch); larger ones
+    # take the grid-stride split.  Every digest against the oracle.
+    msgs = W.uniform_messages(n, length, seed=n + length)
+    out_len = 32 if variant == 5 else [28, 32, 48, 64][variant]
+    got = gpu_uniform(cuda_lib, msgs, length, length, variant, out_len, n)
+    want = oracle_uniform(oracle_mod, msgs, length, length, variant, out_len, n)
+    assert np.array_equal(got, want)
+
+
 def test_uniform_zero_stride_and_single_message(cuda_lib, oracle_mod):
     msgs = W.random_bytes(300, seed=5)
     got = gpu_uniform(cuda_lib, msgs, 0, 300, 3, 64, 37)
