@@ -41,12 +41,20 @@ const void *device_view(const void *p) {
 }
 
 // ---- host-buffer pipeline ---------------------------------------------------
-constexpr int kStages = 3;
+// Three streams, one per role: copies in, hashing, copies out.  A chunk's
+// buffers are reused kStages chunks later; events order each reuse after the
+// work that last read or wrote the buffer, and nothing else, so the copies
+// in run back to back whatever the copies out are doing (a stream per chunk
+// slot would queue a chunk's copy in behind an earlier chunk's copy out).
+constexpr int kStages = 4;
 
 struct Pipeline {
-    cudaStream_t streams[kStages] = {};
+    cudaStream_t in = nullptr, hash = nullptr, out = nullptr;
     uint8_t *d_in[kStages] = {};
     uint8_t *d_out[kStages] = {};
+    cudaEvent_t copied[kStages] = {};   // the copy into d_in[s] is done
+    cudaEvent_t hashed[kStages] = {};   // the hashing of d_in[s] into d_out[s] is done
+    cudaEvent_t drained[kStages] = {};  // the copy out of d_out[s] is done
     size_t in_bytes = 0, out_bytes = 0;
     bool ready = false;
 };
@@ -54,43 +62,68 @@ struct Pipeline {
 std::mutex g_pipe_mu;
 std::map<int, Pipeline> g_pipes;
 
-void free_pipeline(Pipeline &p) {
+void free_buffers(Pipeline &p) {
     for (int s = 0; s < kStages; ++s) {
-        if (p.streams[s]) cudaStreamSynchronize(p.streams[s]);
         if (p.d_in[s]) cudaFree(p.d_in[s]);
         if (p.d_out[s]) cudaFree(p.d_out[s]);
-        if (p.streams[s]) cudaStreamDestroy(p.streams[s]);
-        p.streams[s] = nullptr;
         p.d_in[s] = p.d_out[s] = nullptr;
     }
     p.in_bytes = p.out_bytes = 0;
+}
+
+void sync_pipeline(Pipeline &p) {
+    for (cudaStream_t st : {p.in, p.hash, p.out})
+        if (st) cudaStreamSynchronize(st);
+}
+
+void free_pipeline(Pipeline &p) {
+    sync_pipeline(p);
+    free_buffers(p);
+    for (int s = 0; s < kStages; ++s)
+        for (cudaEvent_t *e : {&p.copied[s], &p.hashed[s], &p.drained[s]})
+            if (*e) {
+                cudaEventDestroy(*e);
+                *e = nullptr;
+            }
+    for (cudaStream_t *st : {&p.in, &p.hash, &p.out})
+        if (*st) {
+            cudaStreamDestroy(*st);
+            *st = nullptr;
+        }
     p.ready = false;
 }
 
 int ensure_pipeline(Pipeline &p, size_t in_bytes, size_t out_bytes) {
     if (!p.ready) {
-        for (int s = 0; s < kStages; ++s)
-            if (cudaStreamCreateWithFlags(&p.streams[s], cudaStreamNonBlocking) != cudaSuccess)
+        for (cudaStream_t *st : {&p.in, &p.hash, &p.out})
+            if (cudaStreamCreateWithFlags(st, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                free_pipeline(p);
                 return KB_ERR_CUDA;
+            }
+        for (int s = 0; s < kStages; ++s)
+            for (cudaEvent_t *e : {&p.copied[s], &p.hashed[s], &p.drained[s]})
+                if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+                    cudaGetLastError();
+                    free_pipeline(p);
+                    return KB_ERR_CUDA;
+                }
         p.ready = true;
     }
     if (p.in_bytes < in_bytes || p.out_bytes < out_bytes) {
+        sync_pipeline(p);
+        const size_t want_in = std::max(p.in_bytes, in_bytes), want_out = std::max(p.out_bytes, out_bytes);
+        free_buffers(p);
         for (int s = 0; s < kStages; ++s) {
-            cudaStreamSynchronize(p.streams[s]);
-            if (p.d_in[s]) cudaFree(p.d_in[s]);
-            if (p.d_out[s]) cudaFree(p.d_out[s]);
-            p.d_in[s] = p.d_out[s] = nullptr;
-        }
-        p.in_bytes = std::max(p.in_bytes, in_bytes);
-        p.out_bytes = std::max(p.out_bytes, out_bytes);
-        for (int s = 0; s < kStages; ++s) {
-            if (cudaMalloc(&p.d_in[s], p.in_bytes ? p.in_bytes : 16) != cudaSuccess ||
-                cudaMalloc(&p.d_out[s], p.out_bytes ? p.out_bytes : 16) != cudaSuccess) {
+            if (cudaMalloc(&p.d_in[s], want_in ? want_in : 16) != cudaSuccess ||
+                cudaMalloc(&p.d_out[s], want_out ? want_out : 16) != cudaSuccess) {
                 cudaGetLastError();
-                free_pipeline(p);
+                free_buffers(p);
                 return KB_ERR_NOMEM;
             }
         }
+        p.in_bytes = want_in;
+        p.out_bytes = want_out;
     }
     return KB_OK;
 }
@@ -259,7 +292,8 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
     cudaEvent_t start;
     if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return KB_ERR_CUDA;
     int rc = cuda_status(cudaEventRecord(start, user));
-    for (int s = 0; s < kStages && rc == KB_OK; ++s) rc = cuda_status(cudaStreamWaitEvent(p.streams[s], start, 0));
+    for (cudaStream_t st : {p.in, p.hash, p.out})
+        if (rc == KB_OK) rc = cuda_status(cudaStreamWaitEvent(st, start, 0));
     // Chunk sizes ramp up from chunk/16 at the start and back down at the
     // end, so that the first copy in and the last copy out, which nothing
     // overlaps, are short.
@@ -283,18 +317,28 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
     uint64_t first = 0;
     for (size_t idx = 0; idx < counts.size() && rc == KB_OK; first += counts[idx], ++idx) {
         const int s = int(idx % kStages);
+        const bool reuse = idx >= size_t(kStages);
         const uint64_t cnt = counts[idx];
         const size_t span = size_t((cnt - 1) * stride + len);
-        if (span) rc = cuda_status(cudaMemcpyAsync(p.d_in[s], h_msgs + first * stride, span,
-                                                   cudaMemcpyHostToDevice, p.streams[s]));
-        if (rc == KB_OK)
-            rc = launch_uniform(p.d_in[s], stride, len, variant, out_len, p.d_out[s], cnt, p.streams[s], *dev);
+        // In: once the hashing of the chunk that last used d_in[s] is done.
+        if (reuse) rc = cuda_status(cudaStreamWaitEvent(p.in, p.hashed[s], 0));
+        if (rc == KB_OK && span)
+            rc = cuda_status(cudaMemcpyAsync(p.d_in[s], h_msgs + first * stride, span, cudaMemcpyHostToDevice, p.in));
+        if (rc == KB_OK) rc = cuda_status(cudaEventRecord(p.copied[s], p.in));
+        // Hash: once this chunk is in and d_out[s] has been copied out.
+        if (rc == KB_OK) rc = cuda_status(cudaStreamWaitEvent(p.hash, p.copied[s], 0));
+        if (rc == KB_OK && reuse) rc = cuda_status(cudaStreamWaitEvent(p.hash, p.drained[s], 0));
+        if (rc == KB_OK) rc = launch_uniform(p.d_in[s], stride, len, variant, out_len, p.d_out[s], cnt, p.hash, *dev);
+        if (rc == KB_OK) rc = cuda_status(cudaEventRecord(p.hashed[s], p.hash));
+        // Out: once this chunk is hashed.
+        if (rc == KB_OK) rc = cuda_status(cudaStreamWaitEvent(p.out, p.hashed[s], 0));
         if (rc == KB_OK && out_len)
             rc = cuda_status(cudaMemcpyAsync(h_digests + first * out_len, p.d_out[s], size_t(cnt * out_len),
-                                             cudaMemcpyDeviceToHost, p.streams[s]));
+                                             cudaMemcpyDeviceToHost, p.out));
+        if (rc == KB_OK) rc = cuda_status(cudaEventRecord(p.drained[s], p.out));
     }
-    for (int s = 0; s < kStages; ++s)
-        if (cudaStreamSynchronize(p.streams[s]) != cudaSuccess) rc = KB_ERR_CUDA;
+    for (cudaStream_t st : {p.in, p.hash, p.out})
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = KB_ERR_CUDA;
     cudaEventDestroy(start);
     return rc;
 }
