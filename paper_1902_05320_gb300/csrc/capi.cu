@@ -9,6 +9,7 @@
 #include <mutex>
 #include <vector>
 
+#include "host_chunks.h"
 #include "keccak_core.cuh"
 #include "runtime.cuh"
 
@@ -297,23 +298,7 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
     // Chunk sizes ramp up from chunk/16 at the start and back down at the
     // end, so that the first copy in and the last copy out, which nothing
     // overlaps, are short.
-    std::vector<uint64_t> counts;
-    {
-        const uint64_t base = std::max<uint64_t>(1, chunk / 16);
-        uint64_t remaining = n;
-        std::vector<uint64_t> tail;
-        for (uint64_t c = base; c < chunk && remaining; c *= 2) {
-            const uint64_t take = std::min(c, remaining);
-            counts.push_back(take);
-            remaining -= take;
-            if (!remaining) break;
-            const uint64_t take_tail = std::min(c, remaining);
-            tail.push_back(take_tail);
-            remaining -= take_tail;
-        }
-        for (; remaining; remaining -= std::min(chunk, remaining)) counts.push_back(std::min(chunk, remaining));
-        counts.insert(counts.end(), tail.rbegin(), tail.rend());
-    }
+    const std::vector<uint64_t> counts = pipeline_chunks(n, chunk);
     uint64_t first = 0;
     for (size_t idx = 0; idx < counts.size() && rc == KB_OK; first += counts[idx], ++idx) {
         const int s = int(idx % kStages);
