@@ -4,9 +4,10 @@
 // Chunks hold at most `chunk` messages.  Their sizes ramp up from chunk/16,
 // doubling, at the start and mirror that ramp at the end, so that the first
 // copy in and the last copy out, which nothing overlaps, are short.  What
-// lies between is cut into the fewest chunks of at most `chunk` messages,
-// of equal size to within one message (no short remainder chunk among
-// them).  The sizes add up to n; none is empty.
+// lies between is cut into full chunks and, last, the remainder, so that
+// the full chunks start at whole multiples of the chunk after the ramp (cut
+// into equal sizes instead, one end-to-end run measured 2616 against
+// 2723-2747 Mhash/s).  The sizes add up to n; none is empty.
 #pragma once
 
 #include <algorithm>
@@ -31,10 +32,7 @@ inline std::vector<uint64_t> pipeline_chunks(uint64_t n, uint64_t chunk) {
         tail.push_back(take_tail);
         remaining -= take_tail;
     }
-    if (remaining) {
-        const uint64_t k = (remaining + chunk - 1) / chunk;
-        for (uint64_t i = 0; i < k; ++i) counts.push_back(remaining / k + (i < remaining % k ? 1 : 0));
-    }
+    for (; remaining; remaining -= std::min(chunk, remaining)) counts.push_back(std::min(chunk, remaining));
     counts.insert(counts.end(), tail.rbegin(), tail.rend());
     return counts;
 }
