@@ -469,7 +469,7 @@ void save_cache_entry(const DeviceInfo &dev, int sc, const QueueConfig &cfg) {
     if (!f) return;
     for (const CacheLine &c : lines)
         std::fprintf(f, kCacheFormat, c.gpu.c_str(), c.sms, c.size_class, c.minb, c.bps);
-    if (std::fclose(f) == 0) std::rename(tmp.c_str(), path);
+    if (std::fclose(f) != 0 || std::rename(tmp.c_str(), path) != 0) std::remove(tmp.c_str());
 }
 
 // SHA3GB_TUNE: "off" ignores tuned configurations, "full" tunes a batch's
