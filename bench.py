@@ -47,8 +47,9 @@ METRIC = "SHA3-256 Mhash/s (64 B msgs)"
 ROUND_OPS_NO_IOTA = 20 + 5 + 50 + 47 + 50
 
 # SMs x 32-bit integer lanes per SM per clock x maximum SM clock: the ALU
-# issue roofline (see the design doc for the derivation and the probe that
-# confirms the lane count).
+# issue roofline.  LOP3 and SHF run on the ALU pipe, which takes one warp
+# instruction per SM sub-partition every two cycles (ncu's pipe counters on
+# the hashing kernel), i.e. 16 lanes per sub-partition and 64 per SM.
 SM_COUNT_GB300 = 152
 INT_LANES_PER_SM_CLK = 64
 SM_MAX_MHZ = 2070.0
