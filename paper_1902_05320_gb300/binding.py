@@ -270,3 +270,59 @@ def int_issue_probe(op: int, iters: int = 4096, stream=None) -> float:
 
 def version() -> str:
     return load().sha3gb_version().decode()
+
+
+# ---- convenience: Python byte strings in, digests out ---------------------------
+def pack_messages(messages, variants=KB_SHA3_256, out_lens=None):
+    """The ragged-batch layout of keccak_batch for a sequence of byte strings:
+    (msgs uint8, offsets uint64, lens uint64, variants uint8, out_lens uint32),
+    messages back to back.  `variants` is one function id or one per message;
+    `out_lens` defaults to the digest size of each SHA3 function and must be
+    given (one value or one per message) for SHAKE."""
+    n = len(messages)
+    views = [np.frombuffer(bytes(m), dtype=np.uint8) for m in messages]
+    lens = np.fromiter((v.size for v in views), dtype=np.uint64, count=n)
+    offsets = np.zeros(n, dtype=np.uint64)
+    if n > 1:
+        np.cumsum(lens[:-1], out=offsets[1:])
+    msgs = np.concatenate(views) if n and int(lens.sum()) else np.zeros(1, dtype=np.uint8)
+    var = np.broadcast_to(np.asarray(variants, dtype=np.int64), (n,))
+    if n and (var.min() < 0 or var.max() > 5):
+        raise ValueError("variants must be function ids 0..5")
+    var = var.astype(np.uint8)
+    if out_lens is None:
+        if n and (var >= 4).any():
+            raise ValueError("SHAKE messages need an out_len")
+        ol = np.array([DIGEST_BYTES[v] for v in var], dtype=np.uint32)
+    else:
+        ol = np.broadcast_to(np.asarray(out_lens, dtype=np.int64), (n,))
+        if n and (ol.min() < 0 or ol.max() > 0xFFFFFFFF):
+            raise ValueError("out_lens must fit in 32 bits")
+        ol = ol.astype(np.uint32)
+        for v, o in zip(var, ol):
+            if v < 4 and o != DIGEST_BYTES[v]:
+                raise ValueError(f"{NAMES[v]} gives {DIGEST_BYTES[v]} bytes, not {o}")
+    return msgs, offsets, lens, var, ol
+
+
+def hash_many(messages, variants=KB_SHA3_256, out_lens=None, stream=None) -> list[bytes]:
+    """Hashes a sequence of byte strings as one ragged batch on the current
+    CUDA device (keccak_batch) and returns their digests, in order."""
+    import torch
+
+    n = len(messages)
+    if n == 0:
+        return []
+    msgs, offsets, lens, var, ol = pack_messages(messages, variants, out_lens)
+    as_dev = lambda a: torch.from_numpy(a.view({8: np.int64, 4: np.int32, 1: np.uint8}[a.itemsize])).cuda()  # noqa
+    d = [as_dev(np.ascontiguousarray(a)) for a in (msgs, offsets, lens, var, ol)]
+    total = int(ol.sum(dtype=np.uint64))
+    out = torch.empty(max(total, 1), dtype=torch.uint8, device="cuda")
+    keccak_batch(*d, out, n, stream)
+    err = keccak_last_error(stream)
+    if err:
+        raise Sha3gbError(-err, f"keccak_batch device status 0x{err:x}")
+    host = out.cpu().numpy()[:total].tobytes()
+    ends = np.cumsum(ol.astype(np.uint64))
+    starts = ends - ol
+    return [host[int(a):int(b)] for a, b in zip(starts, ends)]

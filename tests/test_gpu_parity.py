@@ -562,3 +562,18 @@ def test_keccak_p_every_width_and_round_count(cuda_lib, oracle_mod, b):
         for i in range(n):
             want = oracle_mod.keccak_p(b, nr, _lanes_to_bits(states[i], w))
             assert np.array_equal(_lanes_to_bits(got[i], w), want), (b, nr, i)
+
+
+# -- the binding's byte-string convenience call --------------------------------------------
+def test_hash_many_byte_strings(cuda_lib, oracle_mod):
+    rng = np.random.default_rng(123)
+    lens = [0, 1, 71, 72, 135, 136, 137, 168, 1000, 5000] + list(rng.integers(0, 3000, size=90))
+    messages = [rng.integers(0, 256, size=int(k), dtype=np.uint8).tobytes() for k in lens]
+    variants = [int(v) for v in rng.integers(0, 6, size=len(messages))]
+    out_lens = [W.DIGEST_BYTES[v] if W.DIGEST_BYTES[v] is not None else int(rng.integers(0, 400))
+                for v in variants]
+    got = cuda_lib.hash_many(messages, variants, out_lens)
+    assert got == [oracle_mod.hash(v, m, o) for m, v, o in zip(messages, variants, out_lens)]
+    # One SHA3 function for all, default output sizes.
+    assert cuda_lib.hash_many(messages[:10]) == [oracle_mod.hash(1, m, 32) for m in messages[:10]]
+    assert cuda_lib.hash_many([]) == []
