@@ -372,8 +372,7 @@ uint64_t merkle_nodes(uint64_t n_leaves) {
 
 namespace {
 
-int launch_leaves(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *out, cudaStream_t stream,
-                  const DeviceInfo &dev) {
+int launch_leaves(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *out, cudaStream_t stream) {
     if (n_leaves == 0) return KB_OK;
     const bool a8 = ((reinterpret_cast<uintptr_t>(buf) | leaf_bytes) & 7) == 0 && leaf_bytes > 0;
     // One thread per leaf and as many blocks as that takes: a leaf is a long
@@ -410,13 +409,13 @@ int launch_upper_levels(uint8_t *nodes, uint64_t n, cudaStream_t stream, const D
 
 int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes,
                          cudaStream_t stream, const DeviceInfo &dev) {
-    int rc = launch_leaves(buf, n_leaves, leaf_bytes, nodes, stream, dev);
+    int rc = launch_leaves(buf, n_leaves, leaf_bytes, nodes, stream);
     if (rc != KB_OK) return rc;
     return launch_upper_levels(nodes, n_leaves, stream, dev);
 }
 
 int launch_merkle_many(const uint8_t *buf, uint64_t n_trees, uint64_t leaves_per_tree, uint64_t leaf_bytes,
-                       uint8_t *roots, cudaStream_t stream, const DeviceInfo &dev) {
+                       uint8_t *roots, cudaStream_t stream, const DeviceInfo & /*dev*/) {
     // Leaves on 8-byte boundaries (buffer and leaf size) take the aligned
     // 8-byte loads; others the byte-exact reads.
     const bool a8 = ((reinterpret_cast<uintptr_t>(buf) | leaf_bytes) & 7) == 0;
@@ -441,7 +440,7 @@ int launch_merkle_message(const uint8_t *msg, uint64_t len, uint64_t chunk_bytes
                           cudaStream_t stream, const DeviceInfo &dev) {
     const uint64_t n = merkle_message_leaves(len, chunk_bytes);
     const uint64_t full = len / chunk_bytes;
-    int rc = launch_leaves(msg, full, chunk_bytes, nodes, stream, dev);
+    int rc = launch_leaves(msg, full, chunk_bytes, nodes, stream);
     if (rc != KB_OK) return rc;
     if (full < n) {  // the short (or empty) last chunk
         const uint64_t last = len - full * chunk_bytes;
