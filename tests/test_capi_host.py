@@ -92,3 +92,23 @@ def test_binding_constants_match_the_header():
     assert not missing, missing
     wrong = {k: (v, getattr(binding, k)) for k, v in found.items() if getattr(binding, k) != v}
     assert not wrong, wrong
+
+
+def test_header_is_plain_c(tmp_path):
+    # The boundary is a C ABI: the header compiles as C99 and as C++ on its
+    # own (no CUDA, torch or C++ types), warnings as errors.
+    import os
+    import subprocess
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "use.c"
+    src.write_text('#include "sha3gb.h"\n'
+                   'int use(const uint8_t *m, uint8_t *d, void *s) {\n'
+                   '    int rc = keccak_batch_uniform(m, 64, 64, KB_SHA3_256, 32, d, 1, s);\n'
+                   '    return rc == KB_OK ? keccak_last_error(s) : rc;\n'
+                   '}\n')
+    inc = os.path.join(root, "include")
+    for cmd in (["gcc", "-std=c99", "-pedantic"], ["g++", "-std=c++17", "-x", "c++"]):
+        r = subprocess.run(cmd + ["-Wall", "-Wextra", "-Werror", "-I", inc, "-c", str(src), "-o",
+                                  str(tmp_path / "use.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
