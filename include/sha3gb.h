@@ -450,6 +450,17 @@ int sha3gb_rho_offsets(uint32_t *rho25);
  * and frees a small device buffer. */
 int sha3gb_int_issue_probe(int op, uint32_t iters, double *lanes_per_clk_per_sm, void *stream);
 
+/* Exercises the bounded device wait of the 64-byte staging kernel (its
+ * mbarrier wait for bulk copies) without a fault (diagnostic, not part of the
+ * hashing path): one thread waits for phase 0 of a fresh shared-memory
+ * mbarrier that, with arrive = 0, nothing completes.  The wait gives up after
+ * limit_ns nanoseconds (1 .. 2e9) of the GPU's global timer, sets
+ * KB_DEV_TIMEOUT in the device status word and the kernel returns; the
+ * context stays usable.  With arrive = 1 the thread arrives first and the
+ * wait returns at once.  Stream-ordered; read the result with
+ * keccak_last_error.  KB_ERR_INVALID for arguments out of range. */
+int sha3gb_wait_timeout_probe(uint64_t limit_ns, int arrive, void *stream);
+
 /* Library version string (static storage). */
 const char *sha3gb_version(void);
 

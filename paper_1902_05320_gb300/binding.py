@@ -79,6 +79,7 @@ _SIGS = {
     "keccak_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64]),
     "keccak_tune_get": (ctypes.c_int64, [ctypes.c_int]),
     "sha3gb_int_issue_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
+    "sha3gb_wait_timeout_probe": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]),
 }
 
 
@@ -266,6 +267,13 @@ def int_issue_probe(op: int, iters: int = 4096, stream=None) -> float:
     out = ctypes.c_double()
     _check(load().sha3gb_int_issue_probe(op, iters, ctypes.addressof(out), _stream(stream)), "int_issue_probe")
     return out.value
+
+
+def wait_timeout_probe(limit_ns: int, arrive: bool = False, stream=None) -> None:
+    """Runs the staging kernel's bounded mbarrier wait on a barrier that
+    nothing completes (arrive=False: it gives up after limit_ns and sets
+    KB_DEV_TIMEOUT, read with keccak_last_error) or that completes at once."""
+    _check(load().sha3gb_wait_timeout_probe(limit_ns, int(bool(arrive)), _stream(stream)), "wait_timeout_probe")
 
 
 def version() -> str:

@@ -1,14 +1,19 @@
-// probe.cu -- integer-issue microbenchmark behind the ALU roofline.
+// probe.cu -- diagnostics beside the hashing path:
 //
-// Each thread runs eight interleaved dependency chains of one 32-bit integer
-// instruction (LOP3, SHF funnel rotate, PRMT or IADD3); every block of a
-// one-wave grid reads its SM clock before and after.  Lanes per clock per SM
-// = (instructions x 32 lanes issued on the SM) / elapsed SM cycles.
+// * the integer-issue microbenchmark behind the ALU roofline: each thread runs
+//   eight interleaved dependency chains of one 32-bit integer instruction
+//   (LOP3, SHF funnel rotate, PRMT or IADD3); every block of a one-wave grid
+//   reads its SM clock before and after.  Lanes per clock per SM =
+//   (instructions x 32 lanes issued on the SM) / elapsed SM cycles;
+// * the bounded mbarrier wait of the staging kernel, run on a barrier whose
+//   phase nothing completes, so that its give-up path (KB_DEV_TIMEOUT in the
+//   device status word, then return) is exercised without a fault.
 #include <cuda_runtime.h>
 
 #include <vector>
 
 #include "runtime.cuh"
+#include "tma.cuh"
 
 namespace kb {
 namespace {
@@ -79,10 +84,33 @@ int run_probe(uint32_t iters, double *lanes_per_clk, cudaStream_t stream, const 
     return KB_OK;
 }
 
+// One thread initialises a shared-memory mbarrier for one arrival.  With
+// arrive == 0 nothing ever arrives, so phase 0 never completes and the
+// staging kernel's bounded wait gives up after limit_ns; with arrive == 1 the
+// thread arrives first and the wait returns at once.  No copy or other
+// asynchronous operation is in flight either way, so returning is safe.
+__global__ void k_wait_probe(uint64_t limit_ns, int arrive, unsigned int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+    if (!mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(status, KB_DEV_TIMEOUT);
+}
+
 }  // namespace
 }  // namespace kb
 
 using namespace kb;
+
+extern "C" int sha3gb_wait_timeout_probe(uint64_t limit_ns, int arrive, void *stream) {
+    if (limit_ns == 0 || limit_ns > 2000000000ull || (arrive != 0 && arrive != 1)) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    k_wait_probe<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(limit_ns, arrive, dev->d_status);
+    return cuda_status(cudaGetLastError());
+}
 
 extern "C" int sha3gb_int_issue_probe(int op, uint32_t iters, double *lanes_per_clk_per_sm, void *stream) {
     if (!lanes_per_clk_per_sm || op < 0 || op > 3 || iters == 0) return KB_ERR_INVALID;

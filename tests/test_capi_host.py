@@ -53,6 +53,10 @@ def test_argument_errors_are_returned_before_any_cuda_call(lib):
     assert lib.merkle_sha3_256_levels(1 << 20, 0, 8, 1 << 20, None) == binding.KB_ERR_INVALID
     # Overflowing sizes.
     assert lib.keccak_batch_uniform(1 << 20, 1 << 40, 64, 1, 32, 1 << 20, 1 << 30, None) == binding.KB_ERR_INVALID
+    # The bounded-wait check: a limit of 0 or above 2 s, or arrive not 0/1.
+    assert lib.sha3gb_wait_timeout_probe(0, 0, None) == binding.KB_ERR_INVALID
+    assert lib.sha3gb_wait_timeout_probe(2_000_000_001, 0, None) == binding.KB_ERR_INVALID
+    assert lib.sha3gb_wait_timeout_probe(1000, 2, None) == binding.KB_ERR_INVALID
 
 
 def test_merkle_node_count(lib, oracle_mod):
