@@ -399,7 +399,9 @@ void keccak_release(void);
  *     directly.  Work issued on the legacy default stream or on a stream that
  *     is being captured is always launched directly.
  *   KB_TUNE_AUTOTUNE: 1 (default) uses configurations found by
- *     keccak_batch_autotune for batches of the same size class; 0 ignores them.
+ *     keccak_batch_autotune, in this process or read from the
+ *     SHA3GB_TUNE_CACHE file, for batches of the same size class; 0 ignores
+ *     them (as SHA3GB_TUNE=off does for the whole process).
  *   KB_TUNE_QUEUE_MIN_BLOCKS: register budget of the queue kernel, as the
  *     minimum resident 128-thread blocks per SM it is compiled for (2, 3, 4,
  *     5, 6 or 8; 0 = tuned or default 3).
