@@ -116,3 +116,24 @@ def test_header_is_plain_c(tmp_path):
         r = subprocess.run(cmd + ["-Wall", "-Wextra", "-Werror", "-I", inc, "-c", str(src), "-o",
                                   str(tmp_path / "use.o")], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_binding_signatures_cover_the_header():
+    # Every function the header declares has a ctypes signature in the
+    # binding, with as many arguments as the prototype.
+    import re
+
+    text = open(binding.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_ \*]*?)\b([a-z_][a-z0-9_]*)\s*\(([^;{]*?)\)\s*;", text):
+        name, params = m.group(2), " ".join(m.group(3).split())
+        if name in binding.declared_functions():
+            protos[name] = 0 if params in ("", "void") else params.count(",") + 1
+    assert set(protos) == set(binding.declared_functions())
+    from paper_1902_05320_gb300 import serve
+
+    lib = serve._lib()  # the binding's signatures plus the server's
+    for name, nargs in protos.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None and len(fn.argtypes) == nargs, name
