@@ -537,7 +537,7 @@ def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, auto
         return e0.elapsed_time(e1) / reps
 
     res = {"messages": b.n, "message_bytes": msg_bytes, "permutations": total_perms}
-    saved = [binding.keccak_tune_get(k) for k in range(8)]
+    saved = [binding.keccak_tune_get(k) for k in range(binding.KB_TUNE_KEYS)]
     try:
         binding.keccak_tune_set(binding.KB_TUNE_RAGGED_SCHEDULE, binding.KB_SCHEDULE_INPUT_ORDER)
         ms_in = timed()

@@ -98,7 +98,7 @@ int keccak_batch_uniform(const uint8_t *msgs, uint64_t stride, uint64_t len, int
  * the digest size) cannot be seen on the host without a sync: those messages
  * are skipped (their output bytes are left untouched) and a bit is set in the
  * device status word (see keccak_last_error).  Uses cached internal scratch
- * of 12 bytes per message plus a 4 KiB work-queue descriptor.  The schedule
+ * of 12 bytes per message plus a 46 KiB work-queue descriptor.  The schedule
  * (KB_TUNE_RAGGED_SCHEDULE) changes only the order of the work, never a byte
  * of the output.
  */
@@ -109,13 +109,15 @@ int keccak_batch(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *l
 /*
  * keccak_batch_autotune -- the autotuner of the ragged schedule: hashes the
  * given batch (same arguments and outputs as keccak_batch) once per candidate
- * configuration of the persistent queue kernel (register budget x blocks per
- * SM), checks that every candidate writes the same bytes as the first, and
- * records the fastest for this device and this batch size class (n rounded
- * down to a power of two); later keccak_batch calls of that class use it.
- * Synchronous.  The chosen register budget, blocks per SM and its time in ms
- * are written to the HOST pointers when they are not NULL.  Allocates a
- * temporary device copy of the outputs.
+ * configuration of the persistent queue (register budget x blocks per SM x
+ * staging of message blocks, then threads per message: one thread for every
+ * message, or one warp for each of the K costliest), checks that every
+ * candidate writes the same bytes as the first, and records the fastest for
+ * this device and this batch size class (n rounded down to a power of two);
+ * later keccak_batch calls of that class use it.  Synchronous.  The chosen
+ * register budget, blocks per SM and its time in ms are written to the HOST
+ * pointers when they are not NULL (keccak_batch_autotune_ex reports every
+ * dimension).  Allocates a temporary device copy of the outputs.
  * Environment, read by the library:
  *   SHA3GB_TUNE_CACHE  a file path: configurations the autotuner finds are
  *     written there and read back by later processes on the same kind of GPU.
@@ -134,6 +136,38 @@ int keccak_batch_autotune(const uint8_t *msgs, const uint64_t *offsets, const ui
                           void *stream, int64_t *chosen_min_blocks, int64_t *chosen_blocks_per_sm, float *ms);
 
 /*
+ * One configuration of keccak_batch's queue schedule (Section 4.1's choice of
+ * granularity, made per batch by the autotuner):
+ *   min_blocks     register budget: blocks of 128 threads per SM the kernel
+ *                  is compiled for (2, 3, 4, 5, 6 or 8)
+ *   blocks_per_sm  blocks per SM of the persistent launch (0: as many as fit)
+ *   staging        KB_QUEUE_STAGING_DIRECT, _DIRECT_LOOPED, _ASYNC or _REGS
+ *                  (below)
+ *   warp_messages  threads per message: the warp_messages costliest messages
+ *                  run one warp (32 threads) each, the rest one thread each;
+ *                  0 = one thread for every message
+ *   ms             keccak_batch_autotune_ex: time of the chosen configuration
+ *                  on the tuned batch; 0 elsewhere
+ */
+typedef struct kb_queue_config {
+    int64_t min_blocks;
+    int64_t blocks_per_sm;
+    int64_t staging;
+    int64_t warp_messages;
+    float ms;
+} kb_queue_config;
+
+/* keccak_batch_autotune with every chosen dimension written to *chosen (HOST,
+ * may be NULL). */
+int keccak_batch_autotune_ex(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                             const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
+                             void *stream, kb_queue_config *chosen);
+
+/* The whole configuration keccak_batch would use for n messages on the
+ * current device (as keccak_tuned_config), written to *cfg (HOST). */
+int keccak_tuned_config_ex(uint64_t n, kb_queue_config *cfg);
+
+/*
  * keccak_tuned_config -- the configuration keccak_batch's queue schedule
  * would use for a batch of n messages on the current device, after the
  * tuning knobs, the tuned configurations and the cache file: the register
@@ -147,20 +181,26 @@ int keccak_tuned_config(uint64_t n, int64_t *min_blocks, int64_t *blocks_per_sm)
  * keccak_batch_noalloc -- keccak_batch for callers that cannot allocate
  * device memory.  The paper has no counterpart: it is a deployment variant of
  * the ragged batch entry point above.  keccak_batch allocates its scratch (the
- * digest offsets) with cudaMalloc on first use and whenever a larger batch
- * arrives; a serving process that reserves all device memory up front, a
- * plugin or real-time host where cudaMalloc (which can synchronise the whole
- * device) is not allowed, or code that must know its footprint in advance
- * cannot accept that.  This entry point runs the same kernels with the scratch
- * in a fixed device array compiled into the library, of
- * KB_NOALLOC_MAX_MESSAGES x 8 bytes plus 768 bytes (about 513 KiB), which
- * every GPU that loads the library holds until the process exits.  It never
- * calls cudaMalloc or cudaFree.
+ * work queue's control block, the digest offsets and the work order) with
+ * cudaMalloc on first use and whenever a larger batch arrives; a serving
+ * process that reserves all device memory up front, a plugin or real-time
+ * host where cudaMalloc (which can synchronise the whole device) is not
+ * allowed, or code that must know its footprint in advance cannot accept
+ * that.  This entry point runs keccak_batch's cost-bucketed queue (the same
+ * kernels, in the built-in configuration with one thread per message,
+ * launched directly rather than from a cached graph) with the scratch in a
+ * fixed device array compiled into the library, of KB_NOALLOC_SCRATCH_BYTES
+ * (about 814 KiB: a 256-byte status word, the 46,336-byte control block and
+ * 12 bytes per message plus the scan's tile sums for KB_NOALLOC_MAX_MESSAGES
+ * messages), which every GPU that loads the library holds until the process
+ * exits.  It never calls cudaMalloc or cudaFree.
  *   Arguments and output layout are those of keccak_batch.
  *   n > KB_NOALLOC_MAX_MESSAGES returns KB_ERR_TOO_LARGE and does nothing.
- *   The first call on a device looks up the array's address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before capturing any stream into a CUDA graph.
+ *   The first call in each CUDA context looks up the array's address
+ *   (cudaGetSymbolAddress) with that context current; make that first call
+ *   before capturing any stream into a CUDA graph.  After cudaDeviceReset,
+ *   call keccak_release() before the next call so the address is looked up
+ *   again.
  *   All calls share the one array and each call overwrites it: calls whose
  *   work overlaps on the GPU (several streams or host threads) race, so the
  *   caller must order them.
@@ -169,6 +209,7 @@ int keccak_tuned_config(uint64_t n, int64_t *min_blocks, int64_t *blocks_per_sm)
  *   keccak_last_error.
  */
 #define KB_NOALLOC_MAX_MESSAGES 65536u
+#define KB_NOALLOC_SCRATCH_BYTES 833152u
 int keccak_batch_noalloc(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
                          const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests,
                          uint64_t n, void *stream);
@@ -404,7 +445,7 @@ void keccak_release(void);
  *     them (as SHA3GB_TUNE=off does for the whole process).
  *   KB_TUNE_QUEUE_MIN_BLOCKS: register budget of the queue kernel, as the
  *     minimum resident 128-thread blocks per SM it is compiled for (2, 3, 4,
- *     5, 6 or 8; 0 = tuned or default 3).
+ *     5, 6 or 8; 0 = tuned or default 2).
  *   KB_TUNE_QUEUE_BLOCKS_PER_SM: blocks per SM of the persistent launch
  *     (1..32; 0 = tuned or as many as fit). */
 #define KB_TUNE_RAGGED_SCHEDULE 1
@@ -435,6 +476,28 @@ void keccak_release(void);
 #define KB_TUNE_STAGING 7
 #define KB_STAGING_DIRECT 0
 #define KB_STAGING_TMA 1
+/*   KB_TUNE_QUEUE_STAGING: how keccak_batch's queue kernel reads message
+ *     blocks and which form of the permutation it runs -- 0 (default: tuned,
+ *     else KB_QUEUE_STAGING_REGS), KB_QUEUE_STAGING_DIRECT (each thread loads a block's
+ *     words when it absorbs them; permutation with its last rounds unrolled),
+ *     KB_QUEUE_STAGING_DIRECT_LOOPED (the same with all 24 rounds in a loop,
+ *     half the code), KB_QUEUE_STAGING_ASYNC (looped; each thread's next block
+ *     is copied into shared memory with cp.async while the current
+ *     permutation runs) or KB_QUEUE_STAGING_REGS (looped; the next block is
+ *     loaded into registers before the permutation and absorbed after it).
+ *     The looped forms exist for register budgets 2..4 (KB_QUEUE_STAGING_REGS:
+ *     2 and 3); with another budget the kernel loads directly.
+ *   KB_TUNE_QUEUE_WARP_MESSAGES: threads per message -- -1 (default: tuned,
+ *     else 0) or K >= 0: the K costliest messages of a batch run one warp each
+ *     (the lane-parallel sponge) in a kernel started first on a side stream,
+ *     concurrently with the queue kernel, which takes the rest one thread
+ *     each. */
+#define KB_TUNE_QUEUE_STAGING 8
+#define KB_QUEUE_STAGING_DIRECT 1
+#define KB_QUEUE_STAGING_DIRECT_LOOPED 2
+#define KB_QUEUE_STAGING_ASYNC 3
+#define KB_QUEUE_STAGING_REGS 4
+#define KB_TUNE_QUEUE_WARP_MESSAGES 9
 int keccak_tune_set(int key, int64_t value);
 int64_t keccak_tune_get(int key);
 

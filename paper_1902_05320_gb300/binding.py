@@ -22,6 +22,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "sha3gb.h")
 KB_SHA3_224, KB_SHA3_256, KB_SHA3_384, KB_SHA3_512, KB_SHAKE128, KB_SHAKE256 = 0, 1, 2, 3, 4, 5
 KB_OK, KB_ERR_INVALID, KB_ERR_NOMEM, KB_ERR_CUDA, KB_ERR_TIMEOUT, KB_ERR_TOO_LARGE = 0, -1, -2, -3, -4, -5
 KB_NOALLOC_MAX_MESSAGES = 65536
+KB_NOALLOC_SCRATCH_BYTES = 833152
 KB_DEV_BAD_VARIANT, KB_DEV_BAD_OUTLEN, KB_DEV_TIMEOUT = 0x1, 0x2, 0x4
 DIGEST_BYTES = (28, 32, 48, 64, None, None)
 RATE_BYTES = (144, 136, 104, 72, 168, 136)
@@ -54,6 +55,9 @@ _SIGS = {
                                                                       ctypes.c_void_p]),
     "keccak_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_uint64, ctypes.c_void_p]),
     "keccak_tuned_config": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    "keccak_batch_autotune_ex": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_uint64, ctypes.c_void_p,
+                                                                         ctypes.c_void_p]),
+    "keccak_tuned_config_ex": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_void_p]),
     "keccak_batch_uniform_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                                  ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
                                                  ctypes.c_void_p]),
@@ -140,22 +144,38 @@ def keccak_batch(msgs, offsets, lens, variants, out_lens, digests, n: int, strea
                                _ptr(digests), n, _stream(stream)), "keccak_batch")
 
 
+class QueueConfig(ctypes.Structure):
+    """kb_queue_config of sha3gb.h."""
+    _fields_ = [("min_blocks", ctypes.c_int64), ("blocks_per_sm", ctypes.c_int64), ("staging", ctypes.c_int64),
+                ("warp_messages", ctypes.c_int64), ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {"min_blocks": self.min_blocks, "blocks_per_sm": self.blocks_per_sm,
+                "staging": QUEUE_STAGING_NAMES.get(self.staging, self.staging),
+                "threads_per_message": "1" if self.warp_messages == 0 else
+                f"32 for the {self.warp_messages} costliest, 1 for the rest",
+                "warp_messages": self.warp_messages, "ms": self.ms}
+
+
 def keccak_batch_autotune(msgs, offsets, lens, variants, out_lens, digests, n: int, stream=None) -> dict:
     """Runs the ragged-schedule autotuner on this batch (digests are written
     as by keccak_batch); returns the chosen configuration and its time."""
-    minb, bps, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_float()
-    _check(load().keccak_batch_autotune(_ptr(msgs), _ptr(offsets), _ptr(lens), _ptr(variants), _ptr(out_lens),
-                                        _ptr(digests), n, _stream(stream), ctypes.addressof(minb),
-                                        ctypes.addressof(bps), ctypes.addressof(ms)), "keccak_batch_autotune")
-    return {"min_blocks": minb.value, "blocks_per_sm": bps.value, "ms": ms.value}
+    cfg = QueueConfig()
+    _check(load().keccak_batch_autotune_ex(_ptr(msgs), _ptr(offsets), _ptr(lens), _ptr(variants), _ptr(out_lens),
+                                           _ptr(digests), n, _stream(stream), ctypes.addressof(cfg)),
+           "keccak_batch_autotune_ex")
+    return cfg.as_dict()
 
 
 def keccak_tuned_config(n: int) -> dict:
-    """The register budget and blocks per SM keccak_batch's queue schedule
-    would use for n messages on the current device."""
-    minb, bps = ctypes.c_int64(), ctypes.c_int64()
-    _check(load().keccak_tuned_config(n, ctypes.addressof(minb), ctypes.addressof(bps)), "keccak_tuned_config")
-    return {"min_blocks": minb.value, "blocks_per_sm": bps.value}
+    """The configuration (register budget, blocks per SM, staging, threads per
+    message) keccak_batch's queue schedule would use for n messages on the
+    current device."""
+    cfg = QueueConfig()
+    _check(load().keccak_tuned_config_ex(n, ctypes.addressof(cfg)), "keccak_tuned_config_ex")
+    d = cfg.as_dict()
+    d.pop("ms")
+    return d
 
 
 def keccak_batch_noalloc(msgs, offsets, lens, variants, out_lens, digests, n: int, stream=None) -> None:
@@ -239,6 +259,11 @@ KB_TUNE_HOST_PATH = 6
 KB_HOST_PATH_AUTO, KB_HOST_PATH_STAGED, KB_HOST_PATH_ZERO_COPY = 0, 1, 2
 KB_TUNE_STAGING = 7
 KB_STAGING_DIRECT, KB_STAGING_TMA = 0, 1
+KB_TUNE_QUEUE_STAGING, KB_TUNE_QUEUE_WARP_MESSAGES = 8, 9
+KB_QUEUE_STAGING_DIRECT, KB_QUEUE_STAGING_DIRECT_LOOPED, KB_QUEUE_STAGING_ASYNC, KB_QUEUE_STAGING_REGS = 1, 2, 3, 4
+QUEUE_STAGING_NAMES = {KB_QUEUE_STAGING_DIRECT: "direct", KB_QUEUE_STAGING_DIRECT_LOOPED: "direct_looped",
+                       KB_QUEUE_STAGING_ASYNC: "async", KB_QUEUE_STAGING_REGS: "regs"}
+KB_TUNE_KEYS = 10
 
 
 def keccak_tune_set(key: int, value: int) -> None:

@@ -11,6 +11,7 @@
 
 #include "host_chunks.h"
 #include "keccak_core.cuh"
+#include "queue_host.h"
 #include "runtime.cuh"
 
 namespace kb {
@@ -164,10 +165,9 @@ int keccak_batch(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *l
                          static_cast<cudaStream_t>(stream), *dev);
 }
 
-int keccak_batch_autotune(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
-                          const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
-                          void *stream, int64_t *chosen_min_blocks, int64_t *chosen_blocks_per_sm,
-                          float *ms) {
+int keccak_batch_autotune_ex(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                             const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
+                             void *stream, kb_queue_config *chosen) {
     if (n == 0) return KB_OK;
     if (!msgs || !offsets || !lens || !variant || !out_lens || !digests) return KB_ERR_INVALID;
     if (n > UINT32_MAX) return KB_ERR_INVALID;
@@ -175,16 +175,53 @@ int keccak_batch_autotune(const uint8_t *msgs, const uint64_t *offsets, const ui
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
     NvtxRange range("keccak_batch_autotune");
-    return autotune_ragged_queue(msgs, offsets, lens, variant, out_lens, digests, n,
-                                 static_cast<cudaStream_t>(stream), *dev, chosen_min_blocks, chosen_blocks_per_sm,
-                                 ms);
+    QueueConfig best;
+    const int rc = autotune_ragged_queue(msgs, offsets, lens, variant, out_lens, digests, n,
+                                         static_cast<cudaStream_t>(stream), *dev, &best);
+    if (rc == KB_OK && chosen) {
+        chosen->min_blocks = best.minb;
+        chosen->blocks_per_sm = best.blocks_per_sm;
+        chosen->staging = queue_staging_value(best);
+        chosen->warp_messages = best.warp_messages;
+        chosen->ms = best.ms;
+    }
+    return rc;
 }
 
-int keccak_tuned_config(uint64_t n, int64_t *min_blocks, int64_t *blocks_per_sm) {
+int keccak_batch_autotune(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                          const uint8_t *variant, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
+                          void *stream, int64_t *chosen_min_blocks, int64_t *chosen_blocks_per_sm,
+                          float *ms) {
+    kb_queue_config cfg{};
+    const int rc = keccak_batch_autotune_ex(msgs, offsets, lens, variant, out_lens, digests, n, stream, &cfg);
+    if (rc == KB_OK && n) {
+        if (chosen_min_blocks) *chosen_min_blocks = cfg.min_blocks;
+        if (chosen_blocks_per_sm) *chosen_blocks_per_sm = cfg.blocks_per_sm;
+        if (ms) *ms = cfg.ms;
+    }
+    return rc;
+}
+
+int keccak_tuned_config_ex(uint64_t n, kb_queue_config *cfg) {
+    if (!cfg) return KB_ERR_INVALID;
     int err = KB_OK;
     DeviceInfo *dev = device_info(&err);
     if (!dev) return err;
-    queue_config_for(n, *dev, min_blocks, blocks_per_sm);
+    const QueueConfig c = queue_config_for(n, *dev);
+    cfg->min_blocks = c.minb;
+    cfg->blocks_per_sm = c.blocks_per_sm;
+    cfg->staging = queue_staging_value(c);
+    cfg->warp_messages = c.warp_messages;
+    cfg->ms = 0;
+    return KB_OK;
+}
+
+int keccak_tuned_config(uint64_t n, int64_t *min_blocks, int64_t *blocks_per_sm) {
+    kb_queue_config cfg{};
+    const int rc = keccak_tuned_config_ex(n, &cfg);
+    if (rc != KB_OK) return rc;
+    if (min_blocks) *min_blocks = cfg.min_blocks;
+    if (blocks_per_sm) *blocks_per_sm = cfg.blocks_per_sm;
     return KB_OK;
 }
 
@@ -394,6 +431,7 @@ void keccak_release(void) {
         cudaDeviceSynchronize();
         release_queue_graphs(dev);
         forget_tuning(dev);
+        forget_noalloc_setup();
         std::lock_guard<std::mutex> lk(g_pipe_mu);
         auto it = g_pipes.find(dev);
         if (it != g_pipes.end()) {

@@ -95,13 +95,14 @@ void release_device() {
 }
 
 namespace {
-constexpr int kTuneKeys = 8;
+constexpr int kTuneKeys = 10;
 // Defaults: plain layout, cost-bucketed queue, graphs on, tuned configs used,
 // register budget and blocks per SM from the tuner (or built-in defaults),
 // host buffers staged through device memory, packed 64-byte messages staged
-// through shared memory by bulk copies.
+// through shared memory by bulk copies, queue staging and warp-per-message
+// share from the tuner (or built-in defaults).
 std::atomic<int64_t> g_tuning[kTuneKeys] = {{KB_REP_PLAIN}, {KB_SCHEDULE_QUEUE}, {1}, {1}, {0}, {0},
-                                            {KB_HOST_PATH_AUTO}, {KB_STAGING_TMA}};
+                                            {KB_HOST_PATH_AUTO}, {KB_STAGING_TMA}, {0}, {-1}};
 }  // namespace
 
 int64_t tuning_get(int key) { return (key >= 0 && key < kTuneKeys) ? g_tuning[key].load() : -1; }
@@ -129,6 +130,12 @@ int tuning_set(int key, int64_t value) {
             break;
         case KB_TUNE_STAGING:
             if (value != KB_STAGING_DIRECT && value != KB_STAGING_TMA) return KB_ERR_INVALID;
+            break;
+        case KB_TUNE_QUEUE_STAGING:
+            if (value < 0 || value > KB_QUEUE_STAGING_REGS) return KB_ERR_INVALID;
+            break;
+        case KB_TUNE_QUEUE_WARP_MESSAGES:
+            if (value < -1 || value > int64_t(UINT32_MAX)) return KB_ERR_INVALID;
             break;
         default:
             return KB_ERR_INVALID;

@@ -63,13 +63,6 @@ int launch_uniform(const uint8_t *msgs, uint64_t stride, uint64_t len, int varia
 int launch_ragged(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
                   const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
                   const DeviceInfo &dev);
-// The ragged path on caller-provided scratch: out_off (8 bytes per message),
-// tile_sums (8 bytes per digest_offsets_tiles(n)) and a status word; grid
-// sized from the occupancy API and sm_count, with no library-held state.
-int launch_ragged_external(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
-                           const uint8_t *variants, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
-                           uint64_t *out_off, uint64_t *tile_sums, unsigned int *status, int sm_count,
-                           cudaStream_t stream);
 uint64_t digest_offsets_tiles(uint64_t n);
 int launch_digest_offsets(const uint32_t *out_lens, uint64_t n, uint64_t *out_off, uint64_t *tile_sums,
                           cudaStream_t stream);
@@ -80,18 +73,7 @@ int launch_stream_absorb(uint8_t *states, const uint8_t *msgs, const uint64_t *o
                          uint64_t n, cudaStream_t stream, const DeviceInfo &dev);
 int launch_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
                         cudaStream_t stream, const DeviceInfo &dev);
-// Cost-bucketed persistent path (sha3_queue.cu).
-int launch_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
-                        const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
-                        const DeviceInfo &dev);
-int autotune_ragged_queue(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens, const uint8_t *variants,
-                          const uint32_t *out_lens, uint8_t *digests, uint64_t n, cudaStream_t stream,
-                          const DeviceInfo &dev, int64_t *best_minb, int64_t *best_bps, float *best_ms);
-void release_queue_graphs(int device);
-void forget_tuning(int device);
-// The register budget and blocks per SM keccak_batch's queue schedule would
-// use for n messages on this device (0 blocks per SM: as many as fit).
-void queue_config_for(uint64_t n, const DeviceInfo &dev, int64_t *min_blocks, int64_t *blocks_per_sm);
+// The cost-bucketed persistent path is declared in queue_host.h.
 uint64_t merkle_nodes(uint64_t n_leaves);
 int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes,
                          cudaStream_t stream, const DeviceInfo &dev);

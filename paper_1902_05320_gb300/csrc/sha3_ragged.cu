@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "keccak_core.cuh"
+#include "queue_host.h"
 #include "runtime.cuh"
 #include "scan.cuh"
 #include "sponge.cuh"
@@ -106,26 +107,6 @@ int launch_ragged(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *
     const uint64_t grid = persistent_grid(fn, kThreads, 0, n, dev);
     k_sha3_ragged<<<unsigned(grid), kThreads, 0, stream>>>(msgs, offsets, lens, variants, out_lens, out_off,
                                                            digests, n, dev.d_status);
-    return cuda_status(cudaGetLastError());
-}
-
-int launch_ragged_external(const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
-                           const uint8_t *variants, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
-                           uint64_t *out_off, uint64_t *tile_sums, unsigned int *status, int sm_count,
-                           cudaStream_t stream) {
-    int err = launch_digest_offsets(out_lens, n, out_off, tile_sums, stream);
-    if (err != KB_OK) return err;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sha3_ragged, kThreads, 0) != cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    const uint64_t need = (n + kThreads - 1) / kThreads;
-    const uint64_t full = uint64_t(per_sm) * uint64_t(sm_count > 0 ? sm_count : 1);
-    const uint64_t grid = need < full ? need : full;
-    k_sha3_ragged<<<unsigned(grid), kThreads, 0, stream>>>(msgs, offsets, lens, variants, out_lens, out_off,
-                                                           digests, n, status);
     return cuda_status(cudaGetLastError());
 }
 

@@ -65,14 +65,16 @@ def test_merkle_node_count(lib, oracle_mod):
 
 
 def test_tuning_knobs_validate_values(lib):
-    keys = range(8)
+    keys = range(binding.KB_TUNE_KEYS)
     saved = [binding.keccak_tune_get(k) for k in keys]
     try:
         assert saved[0] == binding.KB_REP_PLAIN and saved[1] == binding.KB_SCHEDULE_QUEUE
-        for key, bad in ((0, 2), (1, 4), (2, 3), (3, -1), (4, 1), (4, 7), (5, 33), (6, 3), (7, 2), (99, 0)):
+        assert saved[binding.KB_TUNE_QUEUE_STAGING] == 0 and saved[binding.KB_TUNE_QUEUE_WARP_MESSAGES] == -1
+        for key, bad in ((0, 2), (1, 4), (2, 3), (3, -1), (4, 1), (4, 7), (5, 33), (6, 3), (7, 2), (8, 5), (8, -1),
+                         (9, -2), (9, 1 << 32), (10, 0), (99, 0)):
             assert lib.keccak_tune_set(key, bad) == binding.KB_ERR_INVALID
         assert binding.keccak_tune_get(99) == -1
-        for key, good in ((0, 1), (1, 0), (2, 0), (3, 0), (4, 6), (5, 3), (6, 1), (7, 1)):
+        for key, good in ((0, 1), (1, 0), (2, 0), (3, 0), (4, 6), (5, 3), (6, 1), (7, 1), (8, 4), (9, 0), (9, 608)):
             binding.keccak_tune_set(key, good)
             assert binding.keccak_tune_get(key) == good
     finally:

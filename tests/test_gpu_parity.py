@@ -414,7 +414,7 @@ def test_interleaved_control_matches_oracle(cuda_lib, oracle_mod):
 # -- ragged schedules, graph replay, autotuner -------------------------------------------
 @pytest.fixture
 def restore_tuning(cuda_lib):
-    keys = range(8)
+    keys = range(cuda_lib.KB_TUNE_KEYS)
     saved = [cuda_lib.keccak_tune_get(k) for k in keys]
     yield
     for k, v in zip(keys, saved):
@@ -432,12 +432,73 @@ def test_ragged_schedules_match_oracle(cuda_lib, oracle_mod, restore_tuning, sch
     assert cuda_lib.keccak_last_error() == 0
 
 
-@pytest.mark.parametrize("min_blocks", [2, 3, 4, 5, 6, 8])
-def test_queue_register_budgets_match_oracle(cuda_lib, oracle_mod, restore_tuning, min_blocks):
+QUEUE_KERNELS = ([(m, 1) for m in (2, 3, 4, 5, 6, 8)] + [(m, s) for s in (2, 3) for m in (2, 3, 4)]
+                 + [(m, 4) for m in (2, 3)])
+
+
+@pytest.mark.parametrize("min_blocks,staging", QUEUE_KERNELS)
+def test_queue_register_budgets_match_oracle(cuda_lib, oracle_mod, restore_tuning, min_blocks, staging):
+    # Every compiled queue kernel: register budget x how it reads message blocks.
     cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_QUEUE_MIN_BLOCKS, min_blocks)
     cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_QUEUE_BLOCKS_PER_SM, 2)
-    b = W.ragged_batch(1500, seed=80 + min_blocks, max_len=2000, gap=2)
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_QUEUE_STAGING, staging)
+    assert cuda_lib.keccak_tuned_config(1500)["staging"] == cuda_lib.QUEUE_STAGING_NAMES[staging]
+    b = W.ragged_batch(1500, seed=80 + min_blocks + 10 * staging, max_len=2000, gap=2)
     assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
+    assert cuda_lib.keccak_last_error() == 0
+
+
+@pytest.mark.parametrize("staging", [1, 2, 3, 4])
+def test_queue_staging_every_padding_case(cuda_lib, oracle_mod, restore_tuning, staging):
+    # Every way the queue kernel reads blocks (direct, direct with the looped
+    # permutation, cp.async into shared memory, registers loaded before the
+    # permutation): every len mod r edge of every variant, multi-block
+    # messages, starts at every byte alignment, SHAKE outputs across squeeze
+    # blocks, in one batch so that warps mix rates at bucket boundaries.
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_QUEUE_STAGING, staging)
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_QUEUE_MIN_BLOCKS, 2)
+    rng = np.random.default_rng(700 + staging)
+    lens, var, ol = [], [], []
+    for v in range(6):
+        r = RATES[v]
+        for L in (0, 1, 3, 4, 5, 7, 8, r - 9, r - 8, r - 2, r - 1, r, r + 1, r + 3, 2 * r - 1, 2 * r, 2 * r + 5,
+                  5 * r + 7, 9 * r):
+            for _ in range(3):
+                lens.append(L)
+                var.append(v)
+                ol.append(DIG[v] if v < 4 else int(rng.choice((0, 1, r - 1, r, r + 1, 3 * r + 2, 512))))
+    order = rng.permutation(len(lens))
+    b = W.ragged_batch(len(lens), seed=710 + staging, gap=7, lens=np.asarray(lens, np.uint64)[order])
+    b.variants = np.asarray(var, np.uint8)[order]
+    b.out_lens = np.asarray(ol, np.uint32)[order]
+    assert len(set(int(o) % 4 for o in b.offsets)) == 4
+    assert np.array_equal(_run_ragged(cuda_lib, b), _oracle_ragged(oracle_mod, b))
+    assert cuda_lib.keccak_last_error() == 0
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+@pytest.mark.parametrize("k", ["0", "1", "32", "all"])
+def test_hybrid_threads_per_message_matches_oracle(cuda_lib, oracle_mod, restore_tuning, k, graphs):
+    # Threads per message: the K costliest messages one warp each (on a side
+    # stream, concurrently with the queue), the rest one thread each.  K = all
+    # puts every message on the warp kernel and leaves the queue empty.
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_GRAPHS, graphs)
+    b = W.ragged_batch(3000, seed=720 + graphs, max_len=20000, gap=3)
+    kk = b.n if k == "all" else int(k)
+    cuda_lib.keccak_tune_set(cuda_lib.KB_TUNE_QUEUE_WARP_MESSAGES, kk)
+    assert cuda_lib.keccak_tuned_config(b.n)["warp_messages"] == kk
+    torch = _torch()
+    s = torch.cuda.Stream()
+    d = [dev(x) for x in (b.msgs, b.offsets, b.lens, b.variants, b.out_lens)]
+    out = torch.full((b.total_out(),), 0xEE, dtype=torch.uint8, device="cuda")
+    want = _oracle_ragged(oracle_mod, b)
+    for _ in range(2):  # the second call replays the captured graph
+        out.fill_(0xEE)
+        torch.cuda.synchronize()
+        cuda_lib.keccak_batch(*d, out, b.n, s)
+        s.synchronize()
+        assert np.array_equal(host(out), want)
+    assert cuda_lib.keccak_last_error(s) == 0
 
 
 def test_graph_replay_reads_current_bytes(cuda_lib, oracle_mod, restore_tuning):
@@ -467,6 +528,9 @@ def test_autotune_keeps_digests(cuda_lib, oracle_mod, restore_tuning):
     out = torch.zeros(b.total_out(), dtype=torch.uint8, device="cuda")
     chosen = cuda_lib.keccak_batch_autotune(*d, out, b.n)
     assert chosen["min_blocks"] in (2, 3, 4, 5, 6, 8) and chosen["blocks_per_sm"] >= 1 and chosen["ms"] > 0
+    assert chosen["staging"] in ("direct", "direct_looped", "async", "regs") and chosen["warp_messages"] in (0, 32, 608)
+    tuned = cuda_lib.keccak_tuned_config(b.n)
+    assert all(tuned[key] == chosen[key] for key in tuned)
     want = _oracle_ragged(oracle_mod, b)
     assert np.array_equal(host(out)[: b.total_out()], want)
     out.zero_()

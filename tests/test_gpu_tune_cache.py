@@ -64,6 +64,22 @@ def _lines(path):
 
 
 SIZE_CLASS = N.bit_length() - 1
+# The built-in configuration (no tuned entry, no knob).
+DEFAULT = {"min_blocks": 2, "blocks_per_sm": 0, "staging": "regs", "threads_per_message": "1", "warp_messages": 0}
+ROW_KEYS = {"gpu", "sms", "size_class", "min_blocks", "blocks_per_sm", "staging", "warp_messages"}
+STAGING = {"direct": 1, "direct_looped": 2, "async": 3, "regs": 4}
+
+
+def _dims(cfg):
+    return {k: cfg[k] for k in DEFAULT}
+
+
+def _row_dims(row):
+    return (row["min_blocks"], row["blocks_per_sm"], row["staging"], row["warp_messages"])
+
+
+def _cfg_dims(cfg):
+    return (cfg["min_blocks"], cfg["blocks_per_sm"], STAGING[cfg["staging"]], cfg["warp_messages"])
 
 
 def test_cache_file_carries_the_tuned_configuration(tmp_path, want):
@@ -71,11 +87,11 @@ def test_cache_file_carries_the_tuned_configuration(tmp_path, want):
     first = _child("autotune", cache)
     assert first["digest"] == want
     chosen = first["chosen"]
-    assert first["after"] == {"min_blocks": chosen["min_blocks"], "blocks_per_sm": chosen["blocks_per_sm"]}
+    assert first["after"] == _dims(chosen)
     rows = _lines(cache)
-    assert len(rows) == 1 and set(rows[0]) == {"gpu", "sms", "size_class", "min_blocks", "blocks_per_sm"}
+    assert len(rows) == 1 and set(rows[0]) == ROW_KEYS
     assert rows[0]["size_class"] == SIZE_CLASS and rows[0]["sms"] >= 1
-    assert (rows[0]["min_blocks"], rows[0]["blocks_per_sm"]) == (chosen["min_blocks"], chosen["blocks_per_sm"])
+    assert _row_dims(rows[0]) == _cfg_dims(chosen)
     # A new process on the same GPU starts from the file.
     second = _child("batch", cache)
     assert second["before"] == first["after"] and second["digest"] == want
@@ -88,20 +104,19 @@ def test_tune_off_ignores_the_cache(tmp_path, want):
     cache = tmp_path / "tune.jsonl"
     first = _child("autotune", cache)
     off = _child("batch", cache, mode="off")
-    assert off["before"] == {"min_blocks": 3, "blocks_per_sm": 0} and off["digest"] == want
+    assert off["before"] == DEFAULT and off["digest"] == want
     assert first["digest"] == want
 
 
 def test_tune_full_tunes_on_first_sight(tmp_path, want):
     cache = tmp_path / "tune.jsonl"
     full = _child("batch", cache, mode="full")
-    assert full["before"] == {"min_blocks": 3, "blocks_per_sm": 0}
+    assert full["before"] == DEFAULT
     assert full["after"]["min_blocks"] in (2, 3, 4, 5, 6, 8) and full["after"]["blocks_per_sm"] >= 1
     assert full["digest"] == want
     rows = _lines(cache)
     assert len(rows) == 1 and rows[0]["size_class"] == SIZE_CLASS
-    assert (rows[0]["min_blocks"], rows[0]["blocks_per_sm"]) == (full["after"]["min_blocks"],
-                                                                  full["after"]["blocks_per_sm"])
+    assert _row_dims(rows[0]) == _cfg_dims(full["after"])
 
 
 def test_malformed_and_foreign_cache_lines_are_ignored(tmp_path, want):
@@ -116,10 +131,24 @@ def test_malformed_and_foreign_cache_lines_are_ignored(tmp_path, want):
                      + json.dumps(dict(entry, sms=row["sms"] + 1, min_blocks=8, blocks_per_sm=1)) + "\n"
                      + json.dumps(dict(entry, min_blocks=7, blocks_per_sm=1)) + "\n"  # not a compiled budget
                      + json.dumps(dict(entry, min_blocks=8, blocks_per_sm=99)) + "\n"  # out of range
+                     + json.dumps(dict(entry, min_blocks=8, staging=3)) + "\n"  # staging not compiled at 8
+                     + json.dumps(dict(entry, min_blocks=2, staging=9)) + "\n"  # no such staging
+                     + json.dumps(dict(entry, min_blocks=2, warp_messages=-5)) + "\n"
                      + '{"gpu": "", "sms": 1}\n')
     r = _child("batch", cache)
-    assert r["before"] == {"min_blocks": 3, "blocks_per_sm": 0} and r["digest"] == want
+    assert r["before"] == DEFAULT and r["digest"] == want
     # The same entry with valid values is taken.
-    cache.write_text(json.dumps(dict(entry, min_blocks=8, blocks_per_sm=1)) + "\n")
+    cache.write_text(json.dumps(dict(entry, min_blocks=8, blocks_per_sm=1, staging=1, warp_messages=0)) + "\n")
     r = _child("batch", cache)
-    assert r["before"] == {"min_blocks": 8, "blocks_per_sm": 1} and r["digest"] == want
+    assert r["before"] == dict(DEFAULT, min_blocks=8, blocks_per_sm=1, staging="direct") and r["digest"] == want
+    cache.write_text(json.dumps(dict(entry, min_blocks=2, blocks_per_sm=1, staging=4, warp_messages=32)) + "\n")
+    r = _child("batch", cache)
+    assert r["before"] == dict(DEFAULT, min_blocks=2, blocks_per_sm=1, staging="regs", warp_messages=32,
+                               threads_per_message="32 for the 32 costliest, 1 for the rest")
+    assert r["digest"] == want
+    # A line in the older form (no staging, no warp_messages) reads as direct
+    # loads with one thread per message.
+    old = {k: entry[k] for k in ("gpu", "sms", "size_class")}
+    cache.write_text(json.dumps(dict(old, min_blocks=4, blocks_per_sm=2)) + "\n")
+    r = _child("batch", cache)
+    assert r["before"] == dict(DEFAULT, min_blocks=4, blocks_per_sm=2, staging="direct") and r["digest"] == want

@@ -3,10 +3,12 @@ allocate device memory (a process under a fixed, pre-reserved memory budget,
 or a host where cudaMalloc's device-wide synchronisation is not allowed).
 
 It must give exactly the digests of keccak_batch, the entry point that keeps
-its scratch in allocated arenas, on two calls in a row: the second call runs
-on the scratch array the first one left behind.  This file is collected last
-so that a run stopping at its first failure has run every other test first.
+its scratch in allocated arenas, and of the CPU oracle, on two calls in a
+row: the second call runs on the scratch array the first one left behind.
+This file is collected last so that a run stopping at its first failure has
+run every other test first.
 """
+import os
 import numpy as np
 import pytest
 
@@ -33,7 +35,11 @@ def _run(torch, lib, fn, b):
     return result
 
 
-def test_noalloc_matches_keccak_batch_on_two_calls_in_a_row():
+def _oracle(oracle_mod, b):
+    return oracle_mod.hash_batch(b.msgs, b.offsets, b.lens, b.variants, b.out_lens, len(os.sched_getaffinity(0)))
+
+
+def test_noalloc_matches_keccak_batch_on_two_calls_in_a_row(oracle_mod):
     import torch
 
     from paper_1902_05320_gb300 import binding
@@ -45,9 +51,38 @@ def test_noalloc_matches_keccak_batch_on_two_calls_in_a_row():
     got2 = _run(torch, lib, lib.keccak_batch_noalloc, second)
     want1 = _run(torch, lib, lib.keccak_batch, first)
     want2 = _run(torch, lib, lib.keccak_batch, second)
-    # Bit-exact, the tolerance of every digest test.
+    # Bit-exact, the tolerance of every digest test, against keccak_batch and
+    # against the oracle.
     assert np.array_equal(got1, want1)
     assert np.array_equal(got2, want2)
+    assert np.array_equal(got1, _oracle(oracle_mod, first))
+    assert np.array_equal(got2, _oracle(oracle_mod, second))
+
+
+def test_noalloc_skips_bad_descriptors(oracle_mod):
+    # Messages with a variant outside 0..5 or a SHA3 output size that is not
+    # the digest size are skipped: their output bytes keep the fill, and every
+    # other message still gets its digest.
+    import torch
+
+    from paper_1902_05320_gb300 import binding
+
+    lib = binding.load()
+    b = W.ragged_batch(3000, seed=904, max_len=4000, gap=2)
+    bad_variant = [5, 700, 2999]
+    sha3 = [i for i in range(b.n) if b.variants[i] < 4 and i not in bad_variant][:3]
+    b.variants[bad_variant] = 9
+    b.out_lens[sha3] += 1
+    got = _run(torch, lib, lib.keccak_batch_noalloc, b)
+    oo = b.out_offsets()
+    good = np.ones(b.n, bool)
+    good[bad_variant + sha3] = False
+    for i in np.flatnonzero(~good):
+        assert (got[int(oo[i]):int(oo[i]) + int(b.out_lens[i])] == 0xEE).all(), i
+    ok = W.RaggedBatch(b.msgs, b.offsets[good], b.lens[good], b.variants[good], b.out_lens[good])
+    want = _oracle(oracle_mod, ok)
+    pieces = [got[int(oo[i]):int(oo[i]) + int(b.out_lens[i])] for i in np.flatnonzero(good)]
+    assert np.array_equal(np.concatenate(pieces), want)
 
 
 def test_noalloc_size_limit_and_empty_batch():
