@@ -345,33 +345,10 @@ def main() -> None:
     # End to end through the host-buffer entry point (copies in the timed region).
     e2e = None
     if not args.no_e2e:
-        h_in = torch.from_numpy(msgs_np).pin_memory()
-        h_out = torch.empty(n_msgs * DIGEST, dtype=torch.uint8).pin_memory()
-        e2e_steps = max(3, min(args.steps, 10))
-        binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, n_msgs, stream)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        for _ in range(e2e_steps):
-            binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, n_msgs, stream)
-        e2e_s = (time.perf_counter() - t) / e2e_steps
-        if not torch.equal(h_out[: 1 << 20], digests[: 1 << 20].cpu()):
-            raise SystemExit("host-buffer path disagrees with the device path")
-        # In place (the kernel reads and writes the page-locked buffers), for comparison.
-        binding.keccak_tune_set(binding.KB_TUNE_HOST_PATH, binding.KB_HOST_PATH_ZERO_COPY)
-        try:
-            t = time.perf_counter()
-            for _ in range(e2e_steps):
-                binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, n_msgs,
-                                                  stream)
-            staged_s = (time.perf_counter() - t) / e2e_steps
-        finally:
-            binding.keccak_tune_set(binding.KB_TUNE_HOST_PATH, binding.KB_HOST_PATH_AUTO)
-        e2e = {"value": world * n_msgs / e2e_s / 1e6, "unit": "Mhash/s", "h2d_bytes_per_step": n_msgs * MSG_BYTES,
-               "d2h_bytes_per_step": n_msgs * DIGEST,
-               "entry_point": "keccak_batch_uniform_host (page-locked buffers, staged copies)",
-               "in_place_zero_copy_mhash_s": world * n_msgs / staged_s / 1e6}
+        e2e = e2e_measurements(binding, torch, stream, msgs_np, digests, n_msgs, world, args.steps)
 
-    extra = {} if args.no_extra else extra_measurements(binding, workloads, torch, stream, msgs, rank)
+    with_oracle = rank == 0 and not args.no_cpu_baseline
+    extra = {} if args.no_extra else extra_measurements(binding, workloads, torch, stream, msgs, rank, with_oracle)
     del msgs, digests
 
     line = {
@@ -405,24 +382,191 @@ def main() -> None:
         dist.destroy_process_group()
 
 
-def extra_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
+def extra_measurements(binding, workloads, torch, stream, msgs, rank, with_oracle=False) -> dict:
     """Secondary figures: the rest of the fixed-length family, then the other
-    workloads (not the headline)."""
-    out = fixed_length_measurements(binding, workloads, torch, stream, msgs, rank)
-    out["small_batches"] = small_batch_measurements(binding, workloads, torch, stream, rank)
-    out["ragged_2p20_loguniform_0_64KiB"] = ragged_measurements(binding, workloads, torch, stream, rank)
-    out["serving_poisson_200k_rps_10s"] = serving_measurements(workloads, torch, rank)
-    out["merkle_4GiB_8KiB_leaves"] = merkle_measurements(binding, workloads, torch, stream, rank)
+    workloads (not the headline), each with the CPU oracle timed beside it on
+    a bounded sample when with_oracle is set."""
+    out = fixed_length_measurements(binding, workloads, torch, stream, msgs, rank, with_oracle)
+    out["small_batches"] = small_batch_measurements(binding, workloads, torch, stream, rank, with_oracle)
+    out["ragged_2p20_loguniform_0_64KiB"] = ragged_measurements(binding, workloads, torch, stream, rank,
+                                                                with_oracle=with_oracle)
+    out["serving_poisson_200k_rps_10s"] = serving_measurements(workloads, torch, rank, with_oracle=with_oracle)
+    out["merkle_4GiB_8KiB_leaves"] = merkle_measurements(binding, workloads, torch, stream, rank,
+                                                         with_oracle=with_oracle)
     out["next_rows"] = next_rows_measurements(binding, workloads, torch, stream, rank)
     try:
         out["int_lanes_per_sm_clk"] = {name: round(binding.int_issue_probe(op, 4096, stream), 2)
-                                       for op, name in enumerate(("lop3", "shf", "prmt", "iadd"))}
+                                       for op, name in enumerate(("lop3_chi", "shf_reg", "prmt_reg", "iadd3"))}
     except Exception as e:  # diagnostic only
         out["int_lanes_per_sm_clk"] = f"probe failed: {e}"
     return out
 
 
-def fixed_length_measurements(binding, workloads, torch, stream, msgs, rank) -> dict:
+# ---------------------------------------------------------------------------
+def oracle_sample(oracle, msgs, offsets, lens, variants, out_lens, perms, seconds, seed, cores=None):
+    """The CPU oracle on a seeded random sample of a batch, sized to about
+    `seconds` of work on the host's cores: returns (sample size, its
+    permutations, elapsed seconds, cores)."""
+    cores = cores or len(os.sched_getaffinity(0))
+    n = len(offsets)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(n)
+    k = min(n, 64 * cores)
+    while True:
+        idx = np.sort(order[:k])
+        t = time.perf_counter()
+        oracle.hash_batch(msgs, offsets[idx], lens[idx], variants[idx], out_lens[idx], cores)
+        dt = time.perf_counter() - t
+        if dt >= 0.25 * seconds or k >= n:
+            return k, int(perms[idx].sum()), dt, cores
+        k = min(n, int(k * min(8.0, max(2.0, seconds / max(dt, 1e-3)))))
+
+
+def oracle_entry(k, n, sample_perms, total_perms, dt, cores, what, unit_rate=None):
+    """An oracle sub-entry: the sample's own rate, and the whole workload's
+    time extrapolated by permutation count (stated as such)."""
+    full_s = dt * total_perms / max(sample_perms, 1)
+    e = {"kind": "oracle", "cores": cores, "sample": f"{k} of {n} {what} (seeded random), {dt:.2f} s",
+         "mperm_s": sample_perms / dt / 1e6, "full_ms_extrapolated": full_s * 1e3,
+         "extrapolation": "sample time x (workload permutations / sample permutations)"}
+    if unit_rate is not None:
+        e.update(unit_rate(k, dt))
+    return e
+
+
+def e2e_measurements(binding, torch, stream, msgs_np, digests, n_msgs, world, steps) -> dict:
+    """The headline workload end to end through keccak_batch_uniform_host on
+    page-locked buffers placed on the GPU's NUMA node, with the host link's
+    copy rates, the buffers' NUMA node and this process's CPUs in the same
+    run, so that the figure can be read against the link that bounds it."""
+    h_in, h_out = binding.HostBuffer(n_msgs * MSG_BYTES), binding.HostBuffer(n_msgs * DIGEST)
+    h_in.array[:] = msgs_np
+    probe_dev = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    link = {}
+    for mode, name in ((0, "copy_engine_h2d_gb_s"), (1, "copy_engine_d2h_gb_s"), (2, "copy_engine_both_ways_gb_s"),
+                       (3, "sm_loads_h2d_gb_s")):
+        try:
+            link[name] = round(binding.host_link_probe(h_in, probe_dev, 256 << 20, mode, 8, stream), 1)
+        except Exception as e:  # diagnostic only
+            link[name] = f"probe failed: {e}"
+    del probe_dev
+    reps = max(3, min(steps, 10))
+
+    def timed(path):
+        binding.keccak_tune_set(binding.KB_TUNE_HOST_PATH, path)
+        try:
+            binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, n_msgs, stream)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for _ in range(reps):
+                binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, n_msgs, stream)
+            return (time.perf_counter() - t) / reps
+        finally:
+            binding.keccak_tune_set(binding.KB_TUNE_HOST_PATH, binding.KB_HOST_PATH_AUTO)
+
+    s_staged = timed(binding.KB_HOST_PATH_STAGED)
+    s_in_place = timed(binding.KB_HOST_PATH_ZERO_COPY)
+    # The default: the first call of this size class decides by a trial.
+    s_auto = timed(binding.KB_HOST_PATH_AUTO)
+    chosen = binding.keccak_host_path_for(n_msgs)
+    if not np.array_equal(h_out.array[: 1 << 20], digests[: 1 << 20].cpu().numpy()):
+        raise SystemExit("host-buffer path disagrees with the device path")
+    nodes = numa_nodes_of_cpus(sorted(os.sched_getaffinity(0)))
+    in_b, out_b = n_msgs * MSG_BYTES, n_msgs * DIGEST
+    res = {"value": world * n_msgs / s_auto / 1e6, "unit": "Mhash/s", "h2d_bytes_per_step": in_b,
+           "d2h_bytes_per_step": out_b,
+           "entry_point": "keccak_batch_uniform_host (KB_HOST_PATH_AUTO; buffers from keccak_host_alloc)",
+           "host_path_chosen": {binding.KB_HOST_PATH_STAGED: "staged", binding.KB_HOST_PATH_ZERO_COPY: "in_place"}.get(
+               chosen, str(chosen)),
+           "staged_mhash_s": n_msgs / s_staged / 1e6, "in_place_mhash_s": n_msgs / s_in_place / 1e6,
+           "link": link,
+           "link_bound_mhash_s": None,
+           "buffers_numa_node": {"messages": h_in.numa_node(), "digests": h_out.numa_node()},
+           "process_cpus": compact_ranges(sorted(os.sched_getaffinity(0))), "process_cpus_numa_nodes": nodes}
+    # The link bound: every step moves in_b + out_b bytes; with both
+    # directions sharing the link at the measured two-way rate, no path can
+    # be faster than this.
+    both = link.get("copy_engine_both_ways_gb_s")
+    if isinstance(both, float) and both > 0:
+        res["link_bound_mhash_s"] = n_msgs / ((in_b + out_b) / (both * 1e9)) / 1e6
+    h_in.free()
+    h_out.free()
+    return res
+
+
+def compact_ranges(xs) -> str:
+    out, start, prev = [], None, None
+    for x in xs:
+        if start is None:
+            start = prev = x
+        elif x == prev + 1:
+            prev = x
+        else:
+            out.append(f"{start}-{prev}" if start != prev else str(start))
+            start = prev = x
+    if start is not None:
+        out.append(f"{start}-{prev}" if start != prev else str(start))
+    return ",".join(out)
+
+
+def numa_nodes_of_cpus(cpus) -> list:
+    nodes = set()
+    base = "/sys/devices/system/node"
+    try:
+        for d in os.listdir(base):
+            if not d.startswith("node"):
+                continue
+            with open(os.path.join(base, d, "cpulist")) as f:
+                text = f.read().strip()
+            mine = set()
+            for part in text.split(","):
+                if "-" in part:
+                    a, b = part.split("-")
+                    mine.update(range(int(a), int(b) + 1))
+                elif part:
+                    mine.add(int(part))
+            if mine & set(cpus):
+                nodes.add(int(d[4:]))
+    except OSError:
+        return []
+    return sorted(nodes)
+
+
+def alu_frac(perms, ms) -> float:
+    """Fraction of the integer-ALU roofline: permutations x the algorithmic ops
+    of one permutation, per second, over the ALU peak."""
+    peak = SM_COUNT_GB300 * INT_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    return perms * ops_per_permutation() / (ms / 1e3) / peak
+
+
+def uniform_oracle(torch, d_msgs, n, length, variant, out_len, seconds, seed, perms_per_msg):
+    """The oracle on a seeded random sample of a fixed-length batch resident on
+    the device (only the sampled messages are copied back)."""
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    cores = len(os.sched_getaffinity(0))
+    k = 64 * cores
+    while True:
+        idx = np.sort(rng.choice(n, min(k, n), replace=False))
+        sample = d_msgs.view(n, length)[torch.from_numpy(idx).cuda()].cpu().numpy().reshape(-1)
+        offs = np.arange(idx.size, dtype=np.uint64) * np.uint64(length)
+        t = time.perf_counter()
+        oracle.hash_batch(sample, offs, np.full(idx.size, length, np.uint64), np.full(idx.size, variant, np.uint8),
+                          np.full(idx.size, out_len, np.uint32), cores)
+        dt = time.perf_counter() - t
+        if dt >= 0.25 * seconds or idx.size >= n:
+            break
+        k = int(k * min(8.0, max(2.0, seconds / max(dt, 1e-3))))
+    return {"kind": "oracle", "cores": cores, "mhash_s": idx.size / dt / 1e6,
+            "sample": f"{idx.size} of {n} messages (seeded random), {dt:.2f} s on {cores} host threads",
+            "full_ms_extrapolated": dt * n / idx.size * 1e3,
+            "extrapolation": "sample time x (messages / sample messages)",
+            "mperm_s": idx.size * perms_per_msg / dt / 1e6}
+
+
+def fixed_length_measurements(binding, workloads, torch, stream, msgs, rank, with_oracle=False) -> dict:
     """2^24 x 64 B with the two state-layout and staging controls and with
     SHA3-512, and 2^22 x 1 KiB SHA3-256."""
     out = {}
@@ -440,6 +584,7 @@ def fixed_length_measurements(binding, workloads, torch, stream, msgs, rank) -> 
         return a.elapsed_time(b) / reps
 
     n = msgs.numel() // MSG_BYTES
+    controls = {}
     # The bit-interleaved state layout, the measured control for the default.
     d32 = torch.empty(n * 32, dtype=torch.uint8, device="cuda")
     binding.keccak_tune_set(binding.KB_TUNE_REPRESENTATION, binding.KB_REP_INTERLEAVED)
@@ -447,25 +592,31 @@ def fixed_length_measurements(binding, workloads, torch, stream, msgs, rank) -> 
         ms = timed(lambda: binding.keccak_batch_uniform(msgs, 64, 64, 1, 32, d32, n, stream))
     finally:
         binding.keccak_tune_set(binding.KB_TUNE_REPRESENTATION, binding.KB_REP_PLAIN)
-    out["sha3_256_2p24_x_64B_interleaved_control_mhash_s"] = n / ms / 1e3
+    controls["interleaved_state_mhash_s"] = n / ms / 1e3
     # Each thread loading its own message, against the default bulk-copy staging.
     binding.keccak_tune_set(binding.KB_TUNE_STAGING, binding.KB_STAGING_DIRECT)
     try:
         ms = timed(lambda: binding.keccak_batch_uniform(msgs, 64, 64, 1, 32, d32, n, stream))
     finally:
         binding.keccak_tune_set(binding.KB_TUNE_STAGING, binding.KB_STAGING_TMA)
-    out["sha3_256_2p24_x_64B_direct_load_control_mhash_s"] = n / ms / 1e3
+    controls["direct_load_mhash_s"] = n / ms / 1e3
+    out["controls_sha3_256_2p24_x_64B"] = controls
     del d32
     d64 = torch.empty(n * 64, dtype=torch.uint8, device="cuda")
     ms = timed(lambda: binding.keccak_batch_uniform(msgs, 64, 64, 3, 64, d64, n, stream))
-    out["sha3_512_2p24_x_64B_mhash_s"] = n / ms / 1e3
+    out["sha3_512_2p24_x_64B"] = {"ms": ms, "mhash_s": n / ms / 1e3, "alu_frac": alu_frac(n, ms)}
+    if with_oracle:
+        out["sha3_512_2p24_x_64B"]["oracle"] = uniform_oracle(torch, msgs, n, 64, 3, 64, 3.0, 11, 1)
     del d64
     n2, l2 = 1 << 22, 1024
     m2 = torch.from_numpy(workloads.uniform_messages(n2, l2, seed=2 + rank)).cuda()
     d2 = torch.empty(n2 * 32, dtype=torch.uint8, device="cuda")
     ms = timed(lambda: binding.keccak_batch_uniform(m2, l2, l2, 1, 32, d2, n2, stream))
-    out["sha3_256_2p22_x_1KiB_mhash_s"] = n2 / ms / 1e3
-    out["sha3_256_2p22_x_1KiB_gb_s"] = n2 * l2 / ms / 1e6
+    perms2 = n2 * (l2 // 136 + 1)
+    out["sha3_256_2p22_x_1KiB"] = {"ms": ms, "mhash_s": n2 / ms / 1e3, "gb_s": n2 * l2 / ms / 1e6,
+                                   "alu_frac": alu_frac(perms2, ms)}
+    if with_oracle:
+        out["sha3_256_2p22_x_1KiB"]["oracle"] = uniform_oracle(torch, m2, n2, l2, 1, 32, 3.0, 12, l2 // 136 + 1)
     del m2, d2
     return out
 
@@ -511,7 +662,7 @@ def config_measurement(config, binding, workloads, torch, rank) -> dict:
 RATES = (144, 136, 104, 72, 168, 136)
 
 
-def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, autotune=True) -> dict:
+def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, autotune=True, with_oracle=False) -> dict:
     """The ragged, mixed-variant batch: 2^20 messages, lengths log-uniform over
     0..64 KiB, variants uniform over the six functions, SHAKE outputs 16..512 B.
     Input-order single launch vs the cost-bucketed persistent queue (graph
@@ -561,9 +712,15 @@ def ragged_measurements(binding, workloads, torch, stream, rank, n=1 << 20, auto
         if ms is None:
             continue
         res[name] = {"ms": ms, "mhash_s": b.n / ms / 1e3, "gb_s": msg_bytes / ms / 1e6,
-                     "gperm_s": total_perms / ms / 1e6}
+                     "gperm_s": total_perms / ms / 1e6, "alu_frac": alu_frac(total_perms, ms)}
     res["autotuned_config"] = tuned
     res["schedules_agree_bytewise"] = same
+    if with_oracle:
+        import oracle
+
+        oracle.build()
+        k, kp, dt, cores = oracle_sample(oracle, b.msgs, b.offsets, b.lens, b.variants, b.out_lens, perms, 5.0, 31)
+        res["oracle"] = oracle_entry(k, b.n, kp, total_perms, dt, cores, "messages")
     return res
 
 
@@ -651,13 +808,15 @@ def next_rows_measurements(binding, workloads, torch, stream, rank) -> dict:
     return res
 
 
-def small_batch_measurements(binding, workloads, torch, stream, rank) -> dict:
+def small_batch_measurements(binding, workloads, torch, stream, rank, with_oracle=False) -> dict:
     """Latency-bound single launches: 4096 x 64 B SHA3-256, and the paper's
     own workload shape (119,040 messages of 10 bytes, the largest point of its
-    Table 3; the paper does not name the variant, SHA3-256 here)."""
+    Table 3; the paper does not name the variant, SHA3-256 here).  The oracle
+    hashes each whole batch."""
     res = {}
     for name, n, length in (("sha3_256_4096_x_64B", 4096, 64), ("sha3_256_119040_x_10B", 119040, 10)):
-        m = torch.from_numpy(workloads.uniform_messages(n, length, seed=10 + rank)).cuda()
+        m_np = workloads.uniform_messages(n, length, seed=10 + rank)
+        m = torch.from_numpy(m_np).cuda()
         d = torch.empty(n * 32, dtype=torch.uint8, device="cuda")
         for _ in range(3):
             binding.keccak_batch_uniform(m, length, length, 1, 32, d, n, stream)
@@ -670,13 +829,28 @@ def small_batch_measurements(binding, workloads, torch, stream, rank) -> dict:
         e1.record(stream)
         torch.cuda.synchronize()
         us = e0.elapsed_time(e1) / reps * 1e3
-        res[name] = {"us_per_launch": us, "mhash_s": n / us, "gb_s": n * length / us / 1e3}
+        res[name] = {"us_per_launch": us, "mhash_s": n / us, "gb_s": n * length / us / 1e3,
+                     "alu_frac": alu_frac(n, us / 1e3)}
+        if with_oracle:
+            import oracle
+
+            oracle.build()
+            cores = len(os.sched_getaffinity(0))
+            offs = np.arange(n, dtype=np.uint64) * np.uint64(length)
+            t = time.perf_counter()
+            oracle.hash_batch(m_np, offs, np.full(n, length, np.uint64), np.full(n, 1, np.uint8),
+                              np.full(n, 32, np.uint32), cores)
+            dt = time.perf_counter() - t
+            res[name]["oracle"] = {"kind": "oracle", "cores": cores, "mhash_s": n / dt / 1e6,
+                                   "us_per_batch": dt * 1e6, "sample": f"the whole batch of {n}, {dt:.2f} s"}
     return res
 
 
-def merkle_measurements(binding, workloads, torch, stream, rank, n_leaves=1 << 19, leaf_bytes=8192) -> dict:
+def merkle_measurements(binding, workloads, torch, stream, rank, n_leaves=1 << 19, leaf_bytes=8192,
+                        with_oracle=False) -> dict:
     """Tree mode: 4 GiB of random bytes in 8 KiB leaves up to the root."""
-    buf = torch.from_numpy(workloads.merkle_buffer(n_leaves, leaf_bytes, seed=4 + rank)).cuda()
+    buf_np = workloads.merkle_buffer(n_leaves, leaf_bytes, seed=4 + rank)
+    buf = torch.from_numpy(buf_np).cuda()
     nodes = torch.empty(32 * binding.merkle_node_count(n_leaves), dtype=torch.uint8, device="cuda")
 
     def run():
@@ -692,17 +866,55 @@ def merkle_measurements(binding, workloads, torch, stream, rank, n_leaves=1 << 1
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    perms = n_leaves * ((leaf_bytes + 1) // 136 + 1) + (binding.merkle_node_count(n_leaves) - n_leaves)
+    leaf_perms = (leaf_bytes + 1) // 136 + 1
+    perms = n_leaves * leaf_perms + (binding.merkle_node_count(n_leaves) - n_leaves)
     t = time.perf_counter()
     root = binding.merkle_sha3_256(buf, n_leaves, leaf_bytes, stream)
     root_ms = (time.perf_counter() - t) * 1e3
     hbm_bytes = n_leaves * leaf_bytes + 32 * binding.merkle_node_count(n_leaves) * 2
-    return {"leaves": n_leaves, "leaf_bytes": leaf_bytes, "ms": ms, "root_call_ms": root_ms,
-            "gb_s": n_leaves * leaf_bytes / ms / 1e6, "gperm_s": perms / ms / 1e6,
-            "hbm_frac_of_measured": hbm_bytes / ms / 1e6 / 6699.8, "root": root.hex()}
+    res = {"leaves": n_leaves, "leaf_bytes": leaf_bytes, "ms": ms, "root_call_ms": root_ms,
+           "gb_s": n_leaves * leaf_bytes / ms / 1e6, "gperm_s": perms / ms / 1e6,
+           "alu_frac": alu_frac(perms, ms), "bound": "alu",
+           "hbm_frac_of_measured": hbm_bytes / ms / 1e6 / measured_hbm_gbs(), "root": root.hex()}
+    del buf, nodes
+    torch.cuda.empty_cache()
+    if with_oracle:
+        import oracle
+
+        oracle.build()
+        # Leaf digests of a seeded sample of leaves (each leaf prefixed 0x00, as
+        # the tree rules have it), the tree's time extrapolated by permutations.
+        rng = np.random.default_rng(41)
+        cores = len(os.sched_getaffinity(0))
+        k = 16 * cores
+        while True:
+            idx = np.sort(rng.choice(n_leaves, min(k, n_leaves), replace=False))
+            sample = np.zeros((idx.size, leaf_bytes + 1), np.uint8)
+            sample[:, 1:] = buf_np.reshape(n_leaves, leaf_bytes)[idx]
+            offs = np.arange(idx.size, dtype=np.uint64) * np.uint64(leaf_bytes + 1)
+            t = time.perf_counter()
+            oracle.hash_batch(sample.reshape(-1), offs, np.full(idx.size, leaf_bytes + 1, np.uint64),
+                              np.full(idx.size, 1, np.uint8), np.full(idx.size, 32, np.uint32), cores)
+            dt = time.perf_counter() - t
+            if dt >= 1.0 or idx.size >= n_leaves:
+                break
+            k = int(k * min(8.0, max(2.0, 4.0 / max(dt, 1e-3))))
+        res["oracle"] = oracle_entry(idx.size, n_leaves, idx.size * leaf_perms, perms, dt, cores,
+                                     "leaves hashed (0x00 || leaf)")
+    return res
 
 
-def serving_measurements(workloads, torch, rank, rate=200_000, seconds=10.0) -> dict:
+def measured_hbm_gbs() -> float:
+    """The measured copy bandwidth of this machine's GPUs when the driver's peaks
+    file is present, else the figure measured on an earlier GB300 run."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6699.8
+
+
+def serving_measurements(workloads, torch, rank, rate=200_000, seconds=10.0, with_oracle=False) -> dict:
     """The serving loop: Poisson arrivals at `rate` requests/s for `seconds`,
     messages log-uniform 32 B..1 MiB from a 4 GiB pinned pool, variants mixed,
     admitted against a 2 GiB device budget."""
@@ -727,6 +939,17 @@ def serving_measurements(workloads, torch, rank, rate=200_000, seconds=10.0) -> 
            "p50_us_small_lt_4KiB": float(np.percentile(lat[wl.lens < 4096], 50) / 1e3),
            "p99_us_small_lt_4KiB": float(np.percentile(lat[wl.lens < 4096], 99) / 1e3),
            "p50_us_large_ge_512KiB": float(np.percentile(lat[big], 50) / 1e3) if big.any() else None}
+    if with_oracle:
+        import oracle
+
+        oracle.build()
+        rates = np.array(RATES, dtype=np.uint64)[wl.variants]
+        perms = (wl.lens // rates + 1 + np.where(wl.out_lens > rates, (wl.out_lens.astype(np.uint64) - 1) // rates, 0))
+        k, kp, dt, cores = oracle_sample(oracle, wl.pool, wl.offsets, wl.lens, wl.variants, wl.out_lens, perms, 8.0, 51)
+        e = oracle_entry(k, wl.n, kp, int(perms.sum()), dt, cores, "requests")
+        # Requests per second the oracle sustains on this mix (by permutations).
+        e["capacity_rps_extrapolated"] = wl.n / (e["full_ms_extrapolated"] / 1e3)
+        res["oracle"] = e
     return res
 
 

@@ -216,11 +216,17 @@ int keccak_batch_noalloc(const uint8_t *msgs, const uint64_t *offsets, const uin
 
 /*
  * keccak_batch_uniform_host -- keccak_batch_uniform on HOST buffers, the whole
- * job including the transfers: the messages are copied to the device, hashed
- * and the digests copied back in chunks pipelined over internal streams
- * (cached device staging buffers), so copies overlap the hashing.  With
- * KB_TUNE_HOST_PATH = KB_HOST_PATH_ZERO_COPY and page-locked buffers the
- * kernel instead works on the host memory in place.  Synchronous: returns when h_digests holds every output.
+ * job including the transfers.  Two paths, chosen by KB_TUNE_HOST_PATH:
+ * staged (the messages are copied to the device, hashed and the digests
+ * copied back in chunks pipelined over internal streams, with cached device
+ * staging buffers, so copies overlap the hashing) or in place (on page-locked
+ * buffers the kernel reads and writes the host memory directly).  With
+ * KB_HOST_PATH_AUTO (the default) and page-locked buffers, the first call of
+ * a size class (n rounded down to a power of two, at least 2^14 messages) on
+ * a device times both paths on parts of its own batch and keeps the faster
+ * for that class (keccak_host_path_for reports the decision); pageable
+ * buffers always take the staged path.  Synchronous: returns when h_digests
+ * holds every output.
  *   h_msgs     host, (n-1)*stride + len bytes
  *   h_digests  host, n*out_len bytes
  * Other arguments as keccak_batch_uniform.  `stream` orders the job after
@@ -228,6 +234,28 @@ int keccak_batch_noalloc(const uint8_t *msgs, const uint64_t *offsets, const uin
  */
 int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t len, int variant,
                               uint32_t out_len, uint8_t *h_digests, uint64_t n, void *stream);
+
+/* The path keccak_batch_uniform_host takes for n messages on the current
+ * device: KB_HOST_PATH_STAGED or KB_HOST_PATH_ZERO_COPY (set by the knob or
+ * decided by a trial), or KB_HOST_PATH_AUTO while undecided; KB_ERR_CUDA
+ * when no device can be used. */
+int keccak_host_path_for(uint64_t n);
+
+/*
+ * keccak_host_alloc -- page-locked host memory for keccak_batch_uniform_host,
+ * placed on the host NUMA node nearest the current device (the device's
+ * cudaDevAttrHostNumaId; no placement where the system reports none or
+ * refuses the binding) and mapped for device access, so that neither path
+ * crosses the link between the host's CPUs.  *ptr receives the HOST address
+ * (NULL on failure).  KB_ERR_INVALID for bytes == 0 or ptr == NULL,
+ * KB_ERR_NOMEM when the memory cannot be mapped or page-locked.
+ * keccak_host_free releases it (KB_ERR_INVALID for a pointer this library did
+ * not return).  keccak_host_numa_node returns the NUMA node holding the page
+ * at ptr, or -1 when the system does not say.
+ */
+int keccak_host_alloc(size_t bytes, void **ptr);
+int keccak_host_free(void *ptr);
+int keccak_host_numa_node(const void *ptr);
 
 /*
  * Streaming (incremental) hashing of n messages at once, for messages that
@@ -458,10 +486,11 @@ void keccak_release(void);
 #define KB_TUNE_QUEUE_MIN_BLOCKS 4
 #define KB_TUNE_QUEUE_BLOCKS_PER_SM 5
 /*   KB_TUNE_HOST_PATH: how keccak_batch_uniform_host moves data --
- *     KB_HOST_PATH_AUTO (default; currently the staged copies, which measure
- *     faster on GB300), KB_HOST_PATH_STAGED (copy in chunks through device
- *     buffers), KB_HOST_PATH_ZERO_COPY (the kernel reads and writes the
- *     page-locked host buffers in place; KB_ERR_INVALID for pageable ones). */
+ *     KB_HOST_PATH_AUTO (default: decided per size class by a timed trial on
+ *     page-locked buffers, staged for pageable ones), KB_HOST_PATH_STAGED
+ *     (copy in chunks through device buffers), KB_HOST_PATH_ZERO_COPY (the
+ *     kernel reads and writes the page-locked host buffers in place;
+ *     KB_ERR_INVALID for pageable ones). */
 #define KB_TUNE_HOST_PATH 6
 #define KB_HOST_PATH_AUTO 0
 #define KB_HOST_PATH_STAGED 1
@@ -508,12 +537,27 @@ int sha3gb_round_constants(uint64_t *rc24);
 int sha3gb_rho_offsets(uint32_t *rho25);
 
 /* Integer-issue microbenchmark for the ALU roofline (diagnostic, not part of
- * the hashing path): runs `iters` x 8 dependent-chain instructions per thread
- * of one kind (op 0 LOP3, 1 SHF funnel rotate, 2 PRMT, 3 32-bit add) on a
- * one-wave grid and writes the measured thread-instructions issued per SM
- * clock to *lanes_per_clk_per_sm (HOST).  Synchronous on `stream`; allocates
- * and frees a small device buffer. */
+ * the hashing path): each thread runs `iters` rounds of 8 instructions of one
+ * kind (op 0 LOP3 with the chi truth table, 1 SHF funnel shift by a register
+ * amount, 2 PRMT with a register selector, 3 three-input 32-bit add), each
+ * instruction taking three values of the previous round, so that no two
+ * rounds fold into one instruction, on a one-wave grid, and writes the
+ * measured thread-instructions issued per SM clock to *lanes_per_clk_per_sm
+ * (HOST).  Synchronous on `stream`; allocates and frees a small device
+ * buffer. */
 int sha3gb_int_issue_probe(int op, uint32_t iters, double *lanes_per_clk_per_sm, void *stream);
+
+/* Host-link diagnostic for the end-to-end figures (not part of the hashing
+ * path): moves `bytes` (a multiple of 16, at least 32) between the HOST
+ * buffer `host` and the DEVICE buffer `device` `reps` times after one untimed
+ * pass and writes the rate in GB/s (10^9 bytes per second) to *gb_s (HOST).
+ * mode 0: copy engine, host to device; 1: copy engine, device to host; 2: the
+ * two directions at once, half of `bytes` each way on two streams; 3: SM
+ * loads of page-locked host memory stored to the device buffer (KB_ERR_INVALID
+ * for pageable memory).  Synchronous on `stream`; the buffers' contents are
+ * overwritten. */
+int sha3gb_host_link_probe(const void *host, void *device, size_t bytes, int mode, int reps, double *gb_s,
+                           void *stream);
 
 /* Exercises the bounded device wait of the 64-byte staging kernel (its
  * mbarrier wait for bulk copies) without a fault (diagnostic, not part of the

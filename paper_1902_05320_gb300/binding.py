@@ -61,6 +61,10 @@ _SIGS = {
     "keccak_batch_uniform_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                                  ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
                                                  ctypes.c_void_p]),
+    "keccak_host_path_for": (ctypes.c_int, [ctypes.c_uint64]),
+    "keccak_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_void_p]),
+    "keccak_host_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "keccak_host_numa_node": (ctypes.c_int, [ctypes.c_void_p]),
     "keccak_stream_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     "keccak_stream_absorb": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_uint64, ctypes.c_void_p]),
     "keccak_stream_final": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_uint64, ctypes.c_void_p]),
@@ -84,6 +88,8 @@ _SIGS = {
     "keccak_tune_get": (ctypes.c_int64, [ctypes.c_int]),
     "sha3gb_int_issue_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
     "sha3gb_wait_timeout_probe": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]),
+    "sha3gb_host_link_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -192,6 +198,41 @@ def keccak_batch_uniform_host(h_msgs, stride: int, length: int, variant: int, ou
                                             n, _stream(stream)), "keccak_batch_uniform_host")
 
 
+def keccak_host_path_for(n: int) -> int:
+    """KB_HOST_PATH_STAGED / _ZERO_COPY chosen for n messages, or _AUTO while undecided."""
+    return _check(load().keccak_host_path_for(n), "keccak_host_path_for")
+
+
+class HostBuffer:
+    """Page-locked host memory on the NUMA node nearest the current device
+    (keccak_host_alloc); ``array`` is a numpy uint8 view of it.  Freed by
+    ``free()`` or when the object is collected."""
+
+    def __init__(self, nbytes: int):
+        p = ctypes.c_void_p()
+        _check(load().keccak_host_alloc(nbytes, ctypes.addressof(p)), "keccak_host_alloc")
+        self.ptr, self.nbytes = int(p.value), nbytes
+        self.array = np.ctypeslib.as_array((ctypes.c_uint8 * nbytes).from_address(self.ptr))
+
+    def data_ptr(self) -> int:
+        return self.ptr
+
+    def numa_node(self) -> int:
+        return int(load().keccak_host_numa_node(self.ptr))
+
+    def free(self) -> None:
+        if self.ptr:
+            self.array = None
+            _check(load().keccak_host_free(self.ptr), "keccak_host_free")
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 KB_STATE_BYTES = 384
 KB_SERVER_LONG_LANE_PARALLEL, KB_SERVER_LONG_THREAD_PER_REQUEST = 0, 1
 
@@ -288,9 +329,19 @@ def rho_offsets() -> list[int]:
 
 def int_issue_probe(op: int, iters: int = 4096, stream=None) -> float:
     """Measured 32-bit integer thread-instructions per SM clock for one kind of
-    instruction: 0 LOP3, 1 SHF, 2 PRMT, 3 add."""
+    instruction: 0 LOP3 (chi table), 1 SHF (register shift), 2 PRMT (register
+    selector), 3 three-input add."""
     out = ctypes.c_double()
     _check(load().sha3gb_int_issue_probe(op, iters, ctypes.addressof(out), _stream(stream)), "int_issue_probe")
+    return out.value
+
+
+def host_link_probe(host, device, nbytes: int, mode: int, reps: int = 5, stream=None) -> float:
+    """GB/s over the host link: mode 0 copy engine host->device, 1 device->host,
+    2 both at once (half each way), 3 SM loads of page-locked host memory."""
+    out = ctypes.c_double()
+    _check(load().sha3gb_host_link_probe(_ptr(host), _ptr(device), nbytes, mode, reps, ctypes.addressof(out),
+                                         _stream(stream)), "sha3gb_host_link_probe")
     return out.value
 
 

@@ -1,10 +1,17 @@
 // probe.cu -- diagnostics beside the hashing path:
 //
-// * the integer-issue microbenchmark behind the ALU roofline: each thread runs
-//   eight interleaved dependency chains of one 32-bit integer instruction
-//   (LOP3, SHF funnel rotate, PRMT or IADD3); every block of a one-wave grid
-//   reads its SM clock before and after.  Lanes per clock per SM =
-//   (instructions x 32 lanes issued on the SM) / elapsed SM cycles;
+// * the integer-issue microbenchmark behind the ALU roofline: each thread
+//   keeps eight 32-bit values and, per round, computes eight new ones, each
+//   from three values of the previous round with one instruction of the kind
+//   measured (LOP3 with the chi table 0xD2, a funnel shift whose amount comes
+//   from a register, PRMT with a register selector, or a three-input add).
+//   Every output depends on three loop-carried inputs and no two rounds can
+//   be merged into one instruction (chi is not linear; the shift amount and
+//   selector change every round), so the compiler issues exactly one
+//   instruction per output, which ncu's smsp__inst_executed confirms.  Every
+//   block of a one-wave grid reads its SM clock before and after.  Lanes per
+//   clock per SM = (instructions x 32 lanes issued on the SM) / elapsed SM
+//   cycles;
 // * the bounded mbarrier wait of the staging kernel, run on a barrier whose
 //   phase nothing completes, so that its give-up path (KB_DEV_TIMEOUT in the
 //   device status word, then return) is exercised without a fault.
@@ -23,10 +30,10 @@ constexpr int kProbeThreads = 256;
 template <int OP>
 __device__ __forceinline__ uint32_t probe_op(uint32_t a, uint32_t b, uint32_t c) {
     uint32_t d;
-    if constexpr (OP == 0) asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    else if constexpr (OP == 1) asm volatile("shf.l.wrap.b32 %0, %1, %2, 7;" : "=r"(d) : "r"(a), "r"(b));
-    else if constexpr (OP == 2) asm volatile("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(d) : "r"(a), "r"(b));
-    else asm volatile("add.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    if constexpr (OP == 0) asm volatile("lop3.b32 %0, %1, %2, %3, 0xD2;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    else if constexpr (OP == 1) asm volatile("shf.l.wrap.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    else if constexpr (OP == 2) asm volatile("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    else asm volatile("add.u32 %0, %1, %2;\n\tadd.u32 %0, %0, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
     return d;
 }
 
@@ -35,14 +42,16 @@ __global__ void __launch_bounds__(kProbeThreads)
     k_int_probe(uint32_t iters, uint32_t seed, uint32_t *sink, long long *cycles) {
     uint32_t a[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = seed * (threadIdx.x + 1) + 0x9E3779B9u * (j + 1);
-    const uint32_t c = seed ^ blockIdx.x;
+    for (int j = 0; j < 8; ++j) a[j] = seed * (threadIdx.x + 1) + 0x9E3779B9u * (j + 1) + blockIdx.x;
     __syncthreads();
     const long long t0 = clock64();
 #pragma unroll 4
     for (uint32_t i = 0; i < iters; ++i) {
+        uint32_t b[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) a[j] = probe_op<OP>(a[j], a[(j + 4) & 7], c + j);
+        for (int j = 0; j < 8; ++j) b[j] = probe_op<OP>(a[j], a[(j + 1) & 7], a[(j + 3) & 7]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = b[j];
     }
     __syncthreads();
     const long long t1 = clock64();

@@ -46,3 +46,29 @@ def test_whole_job_rate_counts_every_rank():
     assert bench.whole_job_mhash_s(1 << 24, 4, 4.0) == 4 * bench.whole_job_mhash_s(1 << 24, 1, 4.0)
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert [bench.rank_seed(1, r) for r in range(3)] == [1, 2, 3]
+
+
+def test_cpu_list_is_compacted_into_ranges():
+    assert bench.compact_ranges([]) == ""
+    assert bench.compact_ranges([0, 1, 2, 3, 7, 9, 10]) == "0-3,7,9-10"
+    assert bench.compact_ranges([5]) == "5"
+
+
+def test_numa_nodes_of_cpus_never_raises():
+    nodes = bench.numa_nodes_of_cpus(sorted(os.sched_getaffinity(0)))
+    assert isinstance(nodes, list) and all(isinstance(n, int) and n >= 0 for n in nodes)
+
+
+def test_oracle_entry_extrapolates_by_permutations():
+    e = bench.oracle_entry(k=100, n=1000, sample_perms=500, total_perms=10_000, dt=2.0, cores=8, what="messages")
+    assert e["full_ms_extrapolated"] == 2.0 * 10_000 / 500 * 1e3
+    assert e["mperm_s"] == 500 / 2.0 / 1e6 and e["cores"] == 8 and e["kind"] == "oracle"
+    assert "100 of 1000 messages" in e["sample"]
+
+
+def test_alu_fraction_of_a_batch_at_the_roofline():
+    # perms x ops at exactly the peak rate is a fraction of 1.
+    peak = bench.SM_COUNT_GB300 * bench.INT_LANES_PER_SM_CLK * bench.SM_MAX_MHZ * 1e6
+    perms = 1_000_000
+    ms = perms * bench.ops_per_permutation() / peak * 1e3
+    assert abs(bench.alu_frac(perms, ms) - 1.0) < 1e-12

@@ -266,7 +266,7 @@ def test_merkle_unaligned_buffer(cuda_lib, oracle_mod):
 
 
 # -- host-buffer pipeline ---------------------------------------------------------------------
-@pytest.mark.parametrize("pinned,path", [(True, 0), (True, 1), (False, 0), (False, 1)])
+@pytest.mark.parametrize("pinned,path", [(True, 0), (True, 1), (True, 2), (False, 0), (False, 1)])
 def test_host_pipeline_matches_oracle(cuda_lib, oracle_mod, pinned, path):
     torch = _torch()
     saved = cuda_lib.keccak_tune_get(cuda_lib.KB_TUNE_HOST_PATH)
@@ -288,6 +288,47 @@ def test_host_pipeline_matches_oracle(cuda_lib, oracle_mod, pinned, path):
                                     np.random.default_rng(1).choice(n, 2000, replace=False)]))
     want = oracle_uniform(oracle_mod, msgs, L, L, 1, 32, n, idx)
     assert np.array_equal(got[idx], want)
+
+
+def test_host_path_trial_and_numa_buffers(cuda_lib, oracle_mod):
+    # KB_HOST_PATH_AUTO on page-locked buffers from keccak_host_alloc: the first
+    # call of a size class hashes a warm-up and a quarter of the batch by each
+    # path, then the rest by the faster; every message must come out exactly
+    # once, across every boundary between the parts, and later calls use the
+    # decision.
+    cuda_lib.keccak_release()  # no earlier decision for this size class
+    n, L = 700_000, 64
+    assert cuda_lib.keccak_host_path_for(n) == cuda_lib.KB_HOST_PATH_AUTO
+    msgs = W.uniform_messages(n, L, seed=52)
+    h_in, h_out = cuda_lib.HostBuffer(n * L), cuda_lib.HostBuffer(n * 32)
+    assert h_in.numa_node() >= -1 and h_out.numa_node() >= -1
+    h_in.array[:] = msgs
+    warm, quarter = n // 64, n // 4
+    edges = [0, warm, 2 * warm, 2 * warm + quarter, 2 * warm + 2 * quarter, n]
+    idx = np.unique(np.concatenate([np.arange(max(0, e - 3), min(n, e + 3)) for e in edges]
+                                   + [np.random.default_rng(3).choice(n, 3000, replace=False)]))
+    want = oracle_uniform(oracle_mod, msgs, L, L, 1, 32, n, idx)
+    for call in range(2):
+        h_out.array[:] = 0xEE
+        cuda_lib.keccak_batch_uniform_host(h_in, L, L, 1, 32, h_out, n)
+        assert np.array_equal(h_out.array.reshape(n, 32)[idx], want), call
+        assert cuda_lib.keccak_host_path_for(n) in (cuda_lib.KB_HOST_PATH_STAGED, cuda_lib.KB_HOST_PATH_ZERO_COPY)
+    h_in.free()
+    h_out.free()
+    cuda_lib.keccak_release()
+    assert cuda_lib.keccak_host_path_for(n) == cuda_lib.KB_HOST_PATH_AUTO
+
+
+def test_host_alloc_arguments(cuda_lib):
+    import ctypes
+
+    lib = cuda_lib.load()
+    p = ctypes.c_void_p()
+    assert lib.keccak_host_alloc(0, ctypes.addressof(p)) == cuda_lib.KB_ERR_INVALID
+    assert lib.keccak_host_alloc(16, None) == cuda_lib.KB_ERR_INVALID
+    assert lib.keccak_host_free(None) == cuda_lib.KB_OK
+    local = np.zeros(64, np.uint8)
+    assert lib.keccak_host_free(local.ctypes.data) == cuda_lib.KB_ERR_INVALID
 
 
 # -- full benchmark sizes, sampled ---------------------------------------------------------------
