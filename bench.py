@@ -483,15 +483,29 @@ def e2e_measurements(binding, torch, stream, msgs_np, digests, n_msgs, world, st
            "link_bound_mhash_s": None,
            "buffers_numa_node": {"messages": h_in.numa_node(), "digests": h_out.numa_node()},
            "process_cpus": compact_ranges(sorted(os.sched_getaffinity(0))), "process_cpus_numa_nodes": nodes}
-    # The link bound: every step moves in_b + out_b bytes; with both
-    # directions sharing the link at the measured two-way rate, no path can
-    # be faster than this.
-    both = link.get("copy_engine_both_ways_gb_s")
-    if isinstance(both, float) and both > 0:
-        res["link_bound_mhash_s"] = n_msgs / ((in_b + out_b) / (both * 1e9)) / 1e6
+    # The link bound: every step moves in_b bytes in and out_b bytes out.
+    # While both directions run they share the link (each at half the
+    # measured two-way rate); the direction with more bytes then finishes
+    # alone at its one-way rate.  No schedule of the copies is shorter.
+    res["link_bound_mhash_s"] = link_bound_mhash_s(link, in_b, out_b, n_msgs)
     h_in.free()
     h_out.free()
     return res
+
+
+def link_bound_mhash_s(link, in_b, out_b, n_msgs):
+    """Hashes per second the host link allows when every step moves in_b bytes
+    to the device and out_b bytes back (both directions overlapped as far as
+    the link lets them), from the link rates measured in the same run."""
+    both, h2d, d2h = (link.get(k) for k in ("copy_engine_both_ways_gb_s", "copy_engine_h2d_gb_s",
+                                             "copy_engine_d2h_gb_s"))
+    if not all(isinstance(x, float) and x > 0 for x in (both, h2d, d2h)):
+        return None
+    each = both / 2 * 1e9  # per direction while both run
+    shared = min(in_b, out_b)
+    rest_rate = (h2d if in_b >= out_b else d2h) * 1e9
+    seconds = shared / each + (max(in_b, out_b) - shared) / rest_rate
+    return n_msgs / seconds / 1e6
 
 
 def compact_ranges(xs) -> str:

@@ -9,14 +9,19 @@
 //   be merged into one instruction (chi is not linear; the shift amount and
 //   selector change every round), so the compiler issues exactly one
 //   instruction per output, which ncu's smsp__inst_executed confirms.  Every
-//   block of a one-wave grid reads its SM clock before and after.  Lanes per
-//   clock per SM = (instructions x 32 lanes issued on the SM) / elapsed SM
-//   cycles;
+//   block of a one-wave grid reads its SM's clock before and after, and the
+//   SM's span is its earliest start to its latest end: the blocks of an SM do
+//   not finish together (the lower hardware warp slots issue first), so an
+//   average of per-block durations would undercount the cycles.  Lanes per
+//   clock per SM = (thread-instructions issued on the SM) / its span;
 // * the bounded mbarrier wait of the staging kernel, run on a barrier whose
 //   phase nothing completes, so that its give-up path (KB_DEV_TIMEOUT in the
 //   device status word, then return) is exercised without a fault.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "runtime.cuh"
@@ -39,7 +44,7 @@ __device__ __forceinline__ uint32_t probe_op(uint32_t a, uint32_t b, uint32_t c)
 
 template <int OP>
 __global__ void __launch_bounds__(kProbeThreads)
-    k_int_probe(uint32_t iters, uint32_t seed, uint32_t *sink, long long *cycles) {
+    k_int_probe(uint32_t iters, uint32_t seed, uint32_t *sink, long long *stamps) {
     uint32_t a[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) a[j] = seed * (threadIdx.x + 1) + 0x9E3779B9u * (j + 1) + blockIdx.x;
@@ -59,7 +64,13 @@ __global__ void __launch_bounds__(kProbeThreads)
 #pragma unroll
     for (int j = 0; j < 8; ++j) x ^= a[j];
     if (x == 0x12345678u) sink[blockIdx.x] = x;  // keeps the chains live
-    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm("mov.u32 %0, %%smid;" : "=r"(smid));
+        stamps[3 * blockIdx.x + 0] = t0;
+        stamps[3 * blockIdx.x + 1] = t1;
+        stamps[3 * blockIdx.x + 2] = smid;
+    }
 }
 
 template <int OP>
@@ -70,26 +81,42 @@ int run_probe(uint32_t iters, double *lanes_per_clk, cudaStream_t stream, const 
         return KB_ERR_CUDA;
     const int grid = per_sm * dev.sm_count;
     uint32_t *sink = nullptr;
-    long long *cycles = nullptr;
+    long long *stamps = nullptr;
     if (cudaMalloc(&sink, sizeof(uint32_t) * grid) != cudaSuccess) return KB_ERR_NOMEM;
-    if (cudaMalloc(&cycles, sizeof(long long) * grid) != cudaSuccess) {
+    if (cudaMalloc(&stamps, 3 * sizeof(long long) * grid) != cudaSuccess) {
         cudaFree(sink);
         return KB_ERR_NOMEM;
     }
-    k_int_probe<OP><<<grid, kProbeThreads, 0, stream>>>(iters, 12345u, sink, cycles);
-    std::vector<long long> h(grid);
+    k_int_probe<OP><<<grid, kProbeThreads, 0, stream>>>(iters, 12345u, sink, stamps);
+    std::vector<long long> h(3 * size_t(grid));
     int rc = cuda_status(cudaGetLastError());
-    if (rc == KB_OK) rc = cuda_status(cudaMemcpyAsync(h.data(), cycles, sizeof(long long) * grid,
+    if (rc == KB_OK) rc = cuda_status(cudaMemcpyAsync(h.data(), stamps, 3 * sizeof(long long) * grid,
                                                       cudaMemcpyDeviceToHost, stream));
     if (rc == KB_OK) rc = cuda_status(cudaStreamSynchronize(stream));
     cudaFree(sink);
-    cudaFree(cycles);
+    cudaFree(stamps);
     if (rc != KB_OK) return rc;
-    double mean = 0;
-    for (long long v : h) mean += double(v);
-    mean /= grid;
-    const double instr_per_sm = double(iters) * 8.0 * kProbeThreads * per_sm;  // thread-instructions
-    *lanes_per_clk = instr_per_sm / mean;
+    // Per SM: its blocks' thread-instructions over its earliest start to latest end.
+    std::map<long long, std::tuple<long long, long long, double>> sms;  // smid -> (first, last, instructions)
+    const double per_block = double(iters) * 8.0 * kProbeThreads;
+    for (int b = 0; b < grid; ++b) {
+        const long long t0 = h[3 * b], t1 = h[3 * b + 1], sm = h[3 * b + 2];
+        auto it = sms.find(sm);
+        if (it == sms.end()) {
+            sms[sm] = std::make_tuple(t0, t1, per_block);
+        } else {
+            auto &[first, last, instr] = it->second;
+            first = std::min(first, t0);
+            last = std::max(last, t1);
+            instr += per_block;
+        }
+    }
+    double sum = 0;
+    for (const auto &kv : sms) {
+        const auto &[first, last, instr] = kv.second;
+        sum += instr / double(std::max<long long>(1, last - first));
+    }
+    *lanes_per_clk = sms.empty() ? 0.0 : sum / double(sms.size());
     return KB_OK;
 }
 

@@ -72,3 +72,13 @@ def test_alu_fraction_of_a_batch_at_the_roofline():
     perms = 1_000_000
     ms = perms * bench.ops_per_permutation() / peak * 1e3
     assert abs(bench.alu_frac(perms, ms) - 1.0) < 1e-12
+
+
+def test_link_bound_overlaps_the_two_directions():
+    link = {"copy_engine_both_ways_gb_s": 340.0, "copy_engine_h2d_gb_s": 210.0, "copy_engine_d2h_gb_s": 130.0}
+    n, in_b, out_b = 1 << 24, 1 << 30, 1 << 29
+    # out_b moves while both directions share the link (170 GB/s each), the
+    # rest of the input alone at 210 GB/s.
+    want = n / (out_b / 170e9 + (in_b - out_b) / 210e9) / 1e6
+    assert abs(bench.link_bound_mhash_s(link, in_b, out_b, n) - want) < 1e-6
+    assert bench.link_bound_mhash_s({"copy_engine_h2d_gb_s": "probe failed"}, in_b, out_b, n) is None
