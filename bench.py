@@ -775,6 +775,14 @@ def next_rows_measurements(binding, workloads, torch, stream, rank) -> dict:
     dig = dev(n * 32)
 
     def stream_run():
+        # k pieces in k calls: the first fused with the initialisation, the
+        # last with the padding and squeeze.
+        binding.keccak_stream_init_absorb(states, variants, buf, offs, lens, n, stream)
+        for _ in range(k - 2):
+            binding.keccak_stream_absorb(states, buf, offs, lens, n, stream)
+        binding.keccak_stream_absorb_final(states, buf, offs, lens, out_lens, dig, n, stream)
+
+    def stream_run_separate():
         binding.keccak_stream_init(states, variants, n, stream)
         for _ in range(k):
             binding.keccak_stream_absorb(states, buf, offs, lens, n, stream)
@@ -782,6 +790,7 @@ def next_rows_measurements(binding, workloads, torch, stream, rank) -> dict:
 
     ms = timed(stream_run)
     res["stream_2p20_states_4x2KiB_sha3_256"] = rates(ms, n * (k * piece // 136 + 1), n * k * piece)
+    res["stream_2p20_states_4x2KiB_sha3_256"]["separate_init_final_ms"] = timed(stream_run_separate)
     # The same 8 KiB per message in one call, for comparison.
     one = dev(n * 8192)
     for j in range(k):
@@ -934,14 +943,27 @@ def serving_measurements(workloads, torch, rank, rate=200_000, seconds=10.0, wit
     admitted against a 2 GiB device budget."""
     from paper_1902_05320_gb300.serve import Server
 
+    from paper_1902_05320_gb300 import binding
+
     wl = workloads.serving_workload(rate, seconds, seed=5 + rank, pool_bytes=4 << 30)
-    pool = torch.empty(wl.pool.size, dtype=torch.uint8, pin_memory=True)
-    pool.copy_(torch.from_numpy(wl.pool))
+    # The message pool and the outputs in page-locked memory on the GPU's NUMA
+    # node (the gather kernel reads the pool over the host link).
+    pool = binding.HostBuffer(wl.pool.size)
+    pool.array[:] = wl.pool
     total = int(wl.out_lens.sum(dtype=np.uint64))
-    outputs = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+    outputs = binding.HostBuffer(max(total, 1))
     lat = np.zeros(wl.n, dtype=np.int64)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
     with Server(hbm_budget_bytes=2 << 30, max_inflight=16, max_batch_requests=4096) as srv:
+        sampler.mark()
         st = srv.replay(pool, wl.offsets, wl.lens, wl.variants, wl.out_lens, wl.arrival_ns, outputs, lat)
+        sampler.mark()
+    sampler.stop()
+    pool_node, out_node = pool.numa_node(), outputs.numa_node()
+    pool.free()
+    outputs.free()
     offered_bytes = int(wl.lens.sum())
     big = wl.lens >= (512 << 10)
     res = {"requests": wl.n, "offered_rps": rate, "offered_gb_s": offered_bytes / seconds / 1e9,
@@ -952,7 +974,8 @@ def serving_measurements(workloads, torch, rank, rate=200_000, seconds=10.0, wit
            "peak_arena_bytes": st["peak_arena_bytes"], "per_request_completion": bool(st["completion_ring"]),
            "p50_us_small_lt_4KiB": float(np.percentile(lat[wl.lens < 4096], 50) / 1e3),
            "p99_us_small_lt_4KiB": float(np.percentile(lat[wl.lens < 4096], 99) / 1e3),
-           "p50_us_large_ge_512KiB": float(np.percentile(lat[big], 50) / 1e3) if big.any() else None}
+           "p50_us_large_ge_512KiB": float(np.percentile(lat[big], 50) / 1e3) if big.any() else None,
+           "pool_numa_node": pool_node, "outputs_numa_node": out_node, "clocks": sampler.summary()}
     if with_oracle:
         import oracle
 

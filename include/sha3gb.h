@@ -280,6 +280,16 @@ int keccak_stream_init(uint8_t *states, const uint8_t *variant, uint64_t n, void
 int keccak_stream_absorb(uint8_t *states, const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
                          uint64_t n, void *stream);
 int keccak_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *digests, uint64_t n, void *stream);
+/* The first and the last step fused with a piece each, so that a message fed
+ * in k pieces takes k calls: keccak_stream_init_absorb initialises the states
+ * (as keccak_stream_init) and absorbs piece i into state i (as
+ * keccak_stream_absorb) in one launch; keccak_stream_absorb_final absorbs
+ * piece i and then finalises (as keccak_stream_final) in one launch.  Same
+ * results as the separate calls. */
+int keccak_stream_init_absorb(uint8_t *states, const uint8_t *variant, const uint8_t *msgs, const uint64_t *offsets,
+                              const uint64_t *lens, uint64_t n, void *stream);
+int keccak_stream_absorb_final(uint8_t *states, const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                               const uint32_t *out_lens, uint8_t *digests, uint64_t n, void *stream);
 
 /*
  * merkle_sha3_256 -- tree mode (Section 4: digests combined pairwise, level

@@ -68,6 +68,8 @@ _SIGS = {
     "keccak_stream_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     "keccak_stream_absorb": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_uint64, ctypes.c_void_p]),
     "keccak_stream_final": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_uint64, ctypes.c_void_p]),
+    "keccak_stream_init_absorb": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_uint64, ctypes.c_void_p]),
+    "keccak_stream_absorb_final": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_uint64, ctypes.c_void_p]),
     "merkle_sha3_256": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
                                        ctypes.c_void_p]),
     "merkle_sha3_256_many": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -249,6 +251,16 @@ def keccak_stream_absorb(states, msgs, offsets, lens, n: int, stream=None) -> No
 def keccak_stream_final(states, out_lens, digests, n: int, stream=None) -> None:
     _check(load().keccak_stream_final(_ptr(states), _ptr(out_lens), _ptr(digests), n, _stream(stream)),
            "keccak_stream_final")
+
+
+def keccak_stream_init_absorb(states, variants, msgs, offsets, lens, n: int, stream=None) -> None:
+    _check(load().keccak_stream_init_absorb(_ptr(states), _ptr(variants), _ptr(msgs), _ptr(offsets), _ptr(lens), n,
+                                            _stream(stream)), "keccak_stream_init_absorb")
+
+
+def keccak_stream_absorb_final(states, msgs, offsets, lens, out_lens, digests, n: int, stream=None) -> None:
+    _check(load().keccak_stream_absorb_final(_ptr(states), _ptr(msgs), _ptr(offsets), _ptr(lens), _ptr(out_lens),
+                                             _ptr(digests), n, _stream(stream)), "keccak_stream_absorb_final")
 
 
 def merkle_sha3_256(buf, n_leaves: int, leaf_bytes: int, stream=None) -> bytes:

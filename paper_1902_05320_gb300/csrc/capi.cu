@@ -227,6 +227,32 @@ int keccak_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *dige
     return launch_stream_final(states, out_lens, digests, n, static_cast<cudaStream_t>(stream), *dev);
 }
 
+int keccak_stream_init_absorb(uint8_t *states, const uint8_t *variant, const uint8_t *msgs, const uint64_t *offsets,
+                              const uint64_t *lens, uint64_t n, void *stream) {
+    if (n == 0) return KB_OK;
+    if (!states || !variant || !msgs || !offsets || !lens || n > UINT64_MAX / KB_STATE_BYTES) return KB_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(states) & 7) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    NvtxRange range("keccak_stream_init_absorb");
+    return launch_stream_step(true, false, states, variant, msgs, offsets, lens, nullptr, nullptr, n,
+                              static_cast<cudaStream_t>(stream), *dev);
+}
+
+int keccak_stream_absorb_final(uint8_t *states, const uint8_t *msgs, const uint64_t *offsets, const uint64_t *lens,
+                               const uint32_t *out_lens, uint8_t *digests, uint64_t n, void *stream) {
+    if (n == 0) return KB_OK;
+    if (!states || !msgs || !offsets || !lens || !out_lens || !digests || n > UINT32_MAX) return KB_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(states) & 7) return KB_ERR_INVALID;
+    int err = KB_OK;
+    DeviceInfo *dev = device_info(&err);
+    if (!dev) return err;
+    NvtxRange range("keccak_stream_absorb_final");
+    return launch_stream_step(false, true, states, nullptr, msgs, offsets, lens, out_lens, digests, n,
+                              static_cast<cudaStream_t>(stream), *dev);
+}
+
 int keccak_p_batch(uint64_t *states, int b, int nr, uint64_t n, void *stream) {
     if (nr < 0 || nr > 1000000) return KB_ERR_INVALID;
     bool width_ok = false;

@@ -9,15 +9,18 @@
 //
 // Kernels: one thread per leaf (the prefixed message is read through a
 // one-byte funnel shift of the leaf's aligned words), then one launch per
-// level with one thread per parent node (0x01 || left || right is exactly one
-// 65-byte block at rate 136) while a level has more than 4096 nodes, and one
-// single-block launch for all the levels above.
+// level (0x01 || left || right is exactly one 65-byte block at rate 136):
+// one thread per parent node while a level has more than 4096 parents, one
+// warp per parent (lane-parallel, about half the latency of a permutation in
+// one thread) below that down to 64 nodes, and one single-block launch, also
+// a warp per parent, for all the levels above.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <climits>
 
 #include "keccak_core.cuh"
+#include "lane_parallel.cuh"
 #include "runtime.cuh"
 #include "sponge.cuh"
 
@@ -190,6 +193,51 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
         merkle_parent(in, count, out, j);
 }
 
+// Parent j of a level of `count` nodes by one warp: the 25 lanes of the
+// state on threads 0..24 (lane_parallel.cuh).  Thread t < 17 builds its
+// 8-byte word of the padded block 0x01 || left || right from two 8-byte words
+// of the children (the children of parent j are the 64 bytes at in + 64j),
+// shifted by the prefix byte; the domain byte follows at byte 65 and 0x80
+// closes the rate at byte 135.  An odd last node is copied up unchanged.
+// Every thread of the warp must call it with the same j.
+__device__ __forceinline__ void merkle_parent_lanes(const LaneCtx &c, const uint8_t *in, uint64_t count, uint8_t *out,
+                                                    uint64_t j) {
+    const int t = c.t;
+    if (2 * j + 1 == count) {  // odd last node: carried up
+        if (t < 4) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(in + 64 * j + 8 * t);
+            *reinterpret_cast<uint2 *>(out + 32 * j + 8 * t) = v;
+        }
+        return;
+    }
+    const uint2 *ch = reinterpret_cast<const uint2 *>(in + 64 * j);
+    uint32_t lo = 0, hi = 0;
+    if (t <= 8) {
+        // Virtual bytes [8t, 8t+8) = child bytes [8t-1, 8t+7).
+        const uint2 cur = t < 8 ? ch[t] : make_uint2(0u, 0u);
+        const uint2 prev = t > 0 ? ch[t - 1] : make_uint2(0u, 0x01u << 24);  // prefix byte at virtual byte 0
+        lo = __funnelshift_l(prev.y, cur.x, 8);
+        hi = __funnelshift_l(cur.x, cur.y, 8);
+        if (t == 8) lo = (prev.y >> 24) | (uint32_t(kDomain) << 8);  // byte 64 = last child byte, 65 = domain
+    }
+    if (t == kRate / 8 - 1) hi ^= 0x80000000u;
+    lane_permute(c, lo, hi);
+    if (t < 4) *reinterpret_cast<uint2 *>(out + 32 * j + 8 * t) = make_uint2(lo, hi);
+}
+
+// One level, one warp per parent (levels of at most kLaneParents parents,
+// where a permutation's latency, not the ALU pipe's throughput, sets the
+// time: the warp form takes about half a thread's latency).
+constexpr uint64_t kLaneParents = 4096;
+
+__global__ void __launch_bounds__(kThreads) k_merkle_level_lanes(const uint8_t *in, uint64_t count, uint8_t *out) {
+    const LaneCtx c = lane_ctx();
+    const uint64_t parents = count / 2 + (count & 1);
+    const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x / 32);
+    for (uint64_t j = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; j < parents; j += warps)
+        merkle_parent_lanes(c, in, count, out, j);
+}
+
 // The top of the tree, from a level of at most kTopCount nodes up to the
 // root, in one block: a block barrier separates the levels (each level is
 // written to global memory, which the barrier makes visible to the block).
@@ -198,14 +246,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
 // starts only where a level is a single permutation's latency anyway (at
 // most 32 parents): from 4096 nodes it took ~165 us, where per-level launches
 // down to 64 nodes and the block from there take ~70 us.
-constexpr int kTopThreads = 64;
+// The block runs one warp per parent (lane-parallel), so its 32 warps take
+// the 32 parents of a 64-node level at once.
+constexpr int kTopThreads = 1024;
 constexpr uint64_t kTopCount = 64;
 
 __global__ void __launch_bounds__(kTopThreads) k_merkle_top(uint8_t *level, uint64_t count) {
+    const LaneCtx c = lane_ctx();
+    const uint64_t warp = threadIdx.x / 32;
     while (count > 1) {
         uint8_t *next = level + 32 * count;
         const uint64_t parents = count / 2 + (count & 1);
-        for (uint64_t j = threadIdx.x; j < parents; j += kTopThreads) merkle_parent(level, count, next, j);
+        for (uint64_t j = warp; j < parents; j += kTopThreads / 32) merkle_parent_lanes(c, level, count, next, j);
         __syncthreads();
         level = next;
         count = parents;
@@ -391,9 +443,14 @@ int launch_upper_levels(uint8_t *nodes, uint64_t n, cudaStream_t stream, const D
     while (n > kTopCount) {
         uint8_t *next = level + 32 * n;
         const uint64_t parents = n / 2 + (n & 1);
-        const uint64_t grid =
-            persistent_grid(reinterpret_cast<const void *>(&k_merkle_level), kThreads, 0, parents, dev);
-        k_merkle_level<<<unsigned(grid), kThreads, 0, stream>>>(level, n, next);
+        if (parents <= kLaneParents) {
+            const uint64_t blocks = (parents + kThreads / 32 - 1) / (kThreads / 32);
+            k_merkle_level_lanes<<<unsigned(blocks), kThreads, 0, stream>>>(level, n, next);
+        } else {
+            const uint64_t grid =
+                persistent_grid(reinterpret_cast<const void *>(&k_merkle_level), kThreads, 0, parents, dev);
+            k_merkle_level<<<unsigned(grid), kThreads, 0, stream>>>(level, n, next);
+        }
         if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
         level = next;
         n = parents;

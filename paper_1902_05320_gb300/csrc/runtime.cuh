@@ -73,6 +73,12 @@ int launch_stream_absorb(uint8_t *states, const uint8_t *msgs, const uint64_t *o
                          uint64_t n, cudaStream_t stream, const DeviceInfo &dev);
 int launch_stream_final(uint8_t *states, const uint32_t *out_lens, uint8_t *digests, uint64_t n,
                         cudaStream_t stream, const DeviceInfo &dev);
+// One fused step: optionally start from fresh states (init, variants read),
+// absorb a piece (msgs may be null for none), optionally pad and squeeze
+// (final_, outputs at the exclusive scan of out_lens).
+int launch_stream_step(bool init, bool final_, uint8_t *states, const uint8_t *variants, const uint8_t *msgs,
+                       const uint64_t *offsets, const uint64_t *lens, const uint32_t *out_lens, uint8_t *digests,
+                       uint64_t n, cudaStream_t stream, const DeviceInfo &dev);
 // The cost-bucketed persistent path is declared in queue_host.h.
 uint64_t merkle_nodes(uint64_t n_leaves);
 int launch_merkle_levels(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, uint8_t *nodes,

@@ -75,3 +75,45 @@ def test_stream_matches_oracle_incremental_form(cuda_lib, oracle_mod):
     cuda_lib.keccak_stream_final(states, torch.tensor([400], dtype=torch.int32, device="cuda"), out, 1)
     torch.cuda.synchronize()
     assert out.cpu().numpy().tobytes() == inc.final(400) == oracle_mod.hash(4, msg.tobytes(), 400)
+
+
+@pytest.mark.parametrize("seed,calls", [(311, 2), (312, 5)])
+def test_fused_first_and_last_steps(cuda_lib, oracle_mod, seed, calls):
+    # keccak_stream_init_absorb takes the first piece with the initialisation
+    # and keccak_stream_absorb_final the last piece with the padding and
+    # squeeze: the digests equal the one-shot hashes, pieces of any length
+    # (empty ones, ones crossing block boundaries, unaligned starts).
+    import torch
+
+    b = W.ragged_batch(500, seed=seed, max_len=4000, gap=5)
+    n = b.n
+    states = torch.zeros(n * cuda_lib.KB_STATE_BYTES, dtype=torch.uint8, device="cuda")
+    d_msgs = _dev(torch, b.msgs)
+    rng = np.random.default_rng(seed)
+    cursor = np.zeros(n, dtype=np.uint64)
+    keep = []
+    out = torch.full((b.total_out(),), 0xEE, dtype=torch.uint8, device="cuda")
+    for c in range(calls):
+        remaining = b.lens - cursor
+        if c == calls - 1:
+            plen = remaining
+        else:
+            plen = (rng.random(n) * remaining.astype(np.float64) * rng.choice([0.0, 0.4, 1.0], size=n)).astype(
+                np.uint64)
+        offs, lens = _dev(torch, b.offsets + cursor), _dev(torch, plen)
+        keep += [offs, lens]
+        if c == 0:
+            cuda_lib.keccak_stream_init_absorb(states, _dev(torch, b.variants), d_msgs, offs, lens, n)
+        elif c == calls - 1:
+            cuda_lib.keccak_stream_absorb_final(states, d_msgs, offs, lens, _dev(torch, b.out_lens), out, n)
+        else:
+            cuda_lib.keccak_stream_absorb(states, d_msgs, offs, lens, n)
+        cursor += plen
+    torch.cuda.synchronize()
+    want = oracle_mod.hash_batch(b.msgs, b.offsets, b.lens, b.variants, b.out_lens, THREADS)
+    assert np.array_equal(out.cpu().numpy(), want)
+    assert cuda_lib.keccak_last_error() == 0
+    # A finalised state refuses a further final step.
+    cuda_lib.keccak_stream_absorb_final(states, d_msgs, _dev(torch, b.offsets), _dev(torch, b.lens),
+                                        _dev(torch, b.out_lens), out, n)
+    assert cuda_lib.keccak_last_error() != 0
