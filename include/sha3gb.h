@@ -262,9 +262,10 @@ int keccak_host_numa_node(const void *ptr);
  * arrive in pieces or are larger than one call should hold: the sponge of
  * Section 3.2 paused between calls.  Each message has a state of
  * KB_STATE_BYTES bytes in device memory (the caller allocates n of them, back
- * to back, 8-byte aligned): its 25 lanes and the bytes of the block not yet
- * complete.  Pieces may have any length; the digest equals the one-shot hash
- * of the concatenated pieces.
+ * to back, 8-byte aligned): its 25 lanes, into which the bytes of the block
+ * not yet complete are already XORed, and the count of those bytes.  Pieces
+ * may have any length; the digest equals the one-shot hash of the
+ * concatenated pieces.
  *   keccak_stream_init: states for variants[i] (device uint8[n]).
  *   keccak_stream_absorb: appends piece i (msgs + offsets[i], lens[i] bytes;
  *     lens[i] = 0 is allowed) to message i.
