@@ -8,19 +8,17 @@
 // (leaf digests first, root last) so that callers can also take proofs.
 //
 // Kernels: one thread per leaf (the prefixed message is read through a
-// one-byte funnel shift of the leaf's aligned words), then one launch per
-// level (0x01 || left || right is exactly one 65-byte block at rate 136):
-// one thread per parent node while a level has more than 4096 parents, one
-// warp per parent (lane-parallel, about half the latency of a permutation in
-// one thread) below that down to 64 nodes, and one single-block launch, also
-// a warp per parent, for all the levels above.
+// one-byte funnel shift of the leaf's aligned words), then the levels above
+// (0x01 || left || right is exactly one 65-byte block at rate 136), one thread
+// per parent node: one launch per level while a level has more than 16384
+// parents, and above that climbing launches that reduce up to six levels
+// each, the upper ones inside each warp through shuffles.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <climits>
 
 #include "keccak_core.cuh"
-#include "lane_parallel.cuh"
 #include "runtime.cuh"
 #include "sponge.cuh"
 
@@ -193,77 +191,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
         merkle_parent(in, count, out, j);
 }
 
-// Parent j of a level of `count` nodes by one warp: the 25 lanes of the
-// state on threads 0..24 (lane_parallel.cuh).  Thread t < 17 builds its
-// 8-byte word of the padded block 0x01 || left || right from two 8-byte words
-// of the children (the children of parent j are the 64 bytes at in + 64j),
-// shifted by the prefix byte; the domain byte follows at byte 65 and 0x80
-// closes the rate at byte 135.  An odd last node is copied up unchanged.
-// Every thread of the warp must call it with the same j.
-__device__ __forceinline__ void merkle_parent_lanes(const LaneCtx &c, const uint8_t *in, uint64_t count, uint8_t *out,
-                                                    uint64_t j) {
-    const int t = c.t;
-    if (2 * j + 1 == count) {  // odd last node: carried up
-        if (t < 4) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(in + 64 * j + 8 * t);
-            *reinterpret_cast<uint2 *>(out + 32 * j + 8 * t) = v;
-        }
-        return;
-    }
-    const uint2 *ch = reinterpret_cast<const uint2 *>(in + 64 * j);
-    uint32_t lo = 0, hi = 0;
-    if (t <= 8) {
-        // Virtual bytes [8t, 8t+8) = child bytes [8t-1, 8t+7).
-        const uint2 cur = t < 8 ? ch[t] : make_uint2(0u, 0u);
-        const uint2 prev = t > 0 ? ch[t - 1] : make_uint2(0u, 0x01u << 24);  // prefix byte at virtual byte 0
-        lo = __funnelshift_l(prev.y, cur.x, 8);
-        hi = __funnelshift_l(cur.x, cur.y, 8);
-        if (t == 8) lo = (prev.y >> 24) | (uint32_t(kDomain) << 8);  // byte 64 = last child byte, 65 = domain
-    }
-    if (t == kRate / 8 - 1) hi ^= 0x80000000u;
-    lane_permute(c, lo, hi);
-    if (t < 4) *reinterpret_cast<uint2 *>(out + 32 * j + 8 * t) = make_uint2(lo, hi);
-}
-
-// One level, one warp per parent (levels of at most kLaneParents parents,
-// where a permutation's latency, not the ALU pipe's throughput, sets the
-// time: the warp form takes about half a thread's latency).
-constexpr uint64_t kLaneParents = 4096;
-
-__global__ void __launch_bounds__(kThreads) k_merkle_level_lanes(const uint8_t *in, uint64_t count, uint8_t *out) {
-    const LaneCtx c = lane_ctx();
-    const uint64_t parents = count / 2 + (count & 1);
-    const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x / 32);
-    for (uint64_t j = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; j < parents; j += warps)
-        merkle_parent_lanes(c, in, count, out, j);
-}
-
-// The top of the tree, from a level of at most kTopCount nodes up to the
-// root, in one block: a block barrier separates the levels (each level is
-// written to global memory, which the barrier makes visible to the block).
-// Levels above that take one launch each over all SMs.  One SM hashes a
-// level of P parents in about P x 68 cycles once P fills it, so the block
-// starts only where a level is a single permutation's latency anyway (at
-// most 32 parents): from 4096 nodes it took ~165 us, where per-level launches
-// down to 64 nodes and the block from there take ~70 us.
-// The block runs one warp per parent (lane-parallel), so its 32 warps take
-// the 32 parents of a 64-node level at once.
-constexpr int kTopThreads = 1024;
-constexpr uint64_t kTopCount = 64;
-
-__global__ void __launch_bounds__(kTopThreads) k_merkle_top(uint8_t *level, uint64_t count) {
-    const LaneCtx c = lane_ctx();
-    const uint64_t warp = threadIdx.x / 32;
-    while (count > 1) {
-        uint8_t *next = level + 32 * count;
-        const uint64_t parents = count / 2 + (count & 1);
-        for (uint64_t j = warp; j < parents; j += kTopThreads / 32) merkle_parent_lanes(c, level, count, next, j);
-        __syncthreads();
-        level = next;
-        count = parents;
-    }
-}
-
 // ---- many small trees, one thread per tree ----------------------------------
 
 // XORs block b of the padded message 0x00 || leaf (leaf_bytes bytes at p, any
@@ -315,6 +242,87 @@ __device__ __forceinline__ void load_node_block(uint32_t (&A)[25], uint32_t (&B)
     }
     PlainRep::set_word(A[8], B[8], (carry >> 24) | (uint32_t(kDomain) << 8), 0u);
     B[kRate / 8 - 1] ^= 0x80000000u;
+}
+
+// Digest (eight little-endian 32-bit words) of SHA3-256(0x01 || l || r).
+__device__ __forceinline__ void node_digest(const uint32_t (&l)[8], const uint32_t (&r)[8], uint32_t (&d)[8]) {
+    uint32_t A[25], B[25];
+    load_node_block(A, B, l, r);
+    PlainRep::permute<true>(A, B);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        d[2 * k] = A[k];
+        d[2 * k + 1] = B[k];
+    }
+}
+
+// Levels where a permutation's latency, not the ALU pipe's throughput, sets
+// the time (at most kClimbParents parents: under one warp per SM
+// sub-partition), up to kClimbLevels + 1 of them in one launch.  Warp w takes
+// parents [32w, 32w + 32) of the first level, one thread each; at climb step
+// l, lane i (a multiple of 2^l) combines its node with that of lane
+// i + 2^(l-1), fetched by a shuffle, into node (32w + i) / 2^l of the next
+// level, or carries it up unchanged when it is that level's odd last node.
+// The warps' ranges nest (the children of nodes [16w, 16w + 16) of a level
+// are nodes [32w, 32w + 32) of the level below), so every node of every level
+// is computed as the level-by-level reduction computes it, and each is
+// written out.  One loop around one permutation call site covers all steps.
+constexpr uint64_t kClimbParents = 16384;
+constexpr int kClimbLevels = 5;
+
+__global__ void __launch_bounds__(kThreads) k_merkle_climb(const uint8_t *in, uint64_t count, uint8_t *out, int climb) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    uint64_t cnt = count;  // nodes of the level being reduced
+    const uint8_t *src = in;
+    uint8_t *dst = out;
+    uint32_t d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int l = 0; l <= climb; ++l) {
+        const uint64_t parents = cnt / 2 + (cnt & 1);
+        uint32_t lft[8], rgt[8];
+        uint64_t q;  // parent index
+        bool act;
+        if (l == 0) {
+            q = warp * 32 + lane;
+            act = q < parents;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) lft[t] = rgt[t] = 0;
+            if (act) {
+                const uint4 *c = reinterpret_cast<const uint4 *>(src + 64 * q);
+                const uint4 a = c[0], b = c[1];
+                lft[0] = a.x, lft[1] = a.y, lft[2] = a.z, lft[3] = a.w;
+                lft[4] = b.x, lft[5] = b.y, lft[6] = b.z, lft[7] = b.w;
+                if (2 * q + 1 < cnt) {
+                    const uint4 e = c[2], f = c[3];
+                    rgt[0] = e.x, rgt[1] = e.y, rgt[2] = e.z, rgt[3] = e.w;
+                    rgt[4] = f.x, rgt[5] = f.y, rgt[6] = f.z, rgt[7] = f.w;
+                }
+            }
+        } else {
+            const uint32_t step = 1u << (l - 1);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                lft[t] = d[t];
+                rgt[t] = __shfl_down_sync(0xFFFFFFFFu, d[t], step);
+            }
+            const uint64_t c = warp * (32u >> (l - 1)) + (lane >> (l - 1));  // this lane's node: the left child
+            act = (lane & (2 * step - 1)) == 0 && c < cnt;
+            q = c >> 1;
+        }
+        if (act) {
+            if (2 * q + 1 < cnt) node_digest(lft, rgt, d);
+            else {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) d[t] = lft[t];  // odd last node: carried up
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(dst + 32 * q);
+            o[0] = make_uint4(d[0], d[1], d[2], d[3]);
+            o[1] = make_uint4(d[4], d[5], d[6], d[7]);
+        }
+        src = dst;
+        dst += 32 * parents;
+        cnt = parents;
+    }
 }
 
 // Stack of subtree digests: sizes are distinct powers of two (the binary
@@ -437,27 +445,33 @@ int launch_leaves(const uint8_t *buf, uint64_t n_leaves, uint64_t leaf_bytes, ui
     return cuda_status(cudaGetLastError());
 }
 
-// Every level above the n leaf digests at `nodes`, written after them.
+// Every level above the n leaf digests at `nodes`, written after them: one
+// launch per level while a level has more than kClimbParents parents (there
+// the ALU pipe's throughput sets the time), then climbing launches of up to
+// kClimbLevels + 1 levels each.
 int launch_upper_levels(uint8_t *nodes, uint64_t n, cudaStream_t stream, const DeviceInfo &dev) {
     uint8_t *level = nodes;
-    while (n > kTopCount) {
-        uint8_t *next = level + 32 * n;
+    while (n > 1) {
         const uint64_t parents = n / 2 + (n & 1);
-        if (parents <= kLaneParents) {
-            const uint64_t blocks = (parents + kThreads / 32 - 1) / (kThreads / 32);
-            k_merkle_level_lanes<<<unsigned(blocks), kThreads, 0, stream>>>(level, n, next);
-        } else {
+        if (parents > kClimbParents) {
             const uint64_t grid =
                 persistent_grid(reinterpret_cast<const void *>(&k_merkle_level), kThreads, 0, parents, dev);
-            k_merkle_level<<<unsigned(grid), kThreads, 0, stream>>>(level, n, next);
+            k_merkle_level<<<unsigned(grid), kThreads, 0, stream>>>(level, n, level + 32 * n);
+            if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
+            level += 32 * n;
+            n = parents;
+            continue;
         }
+        int climb = 0;
+        for (uint64_t m = parents; climb < kClimbLevels && m > 1; m = m / 2 + (m & 1)) ++climb;
+        const uint64_t threads = (parents + 31) / 32 * 32;
+        const uint64_t blocks = (threads + kThreads - 1) / kThreads;
+        k_merkle_climb<<<unsigned(blocks), kThreads, 0, stream>>>(level, n, level + 32 * n, climb);
         if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
-        level = next;
-        n = parents;
-    }
-    if (n > 1) {
-        k_merkle_top<<<1, kTopThreads, 0, stream>>>(level, n);
-        if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
+        for (int l = 0; l <= climb; ++l) {
+            level += 32 * n;
+            n = n / 2 + (n & 1);
+        }
     }
     return KB_OK;
 }

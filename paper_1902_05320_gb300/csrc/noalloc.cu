@@ -72,10 +72,14 @@ CUcontext current_context() {
 int setup(Setup *out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return KB_ERR_CUDA;
-    // Makes the device's primary context current when nothing is yet.
-    if (cudaFree(nullptr) != cudaSuccess) return KB_ERR_CUDA;
-    const CUcontext ctx = current_context();
-    if (!ctx) return KB_ERR_CUDA;
+    CUcontext ctx = current_context();
+    if (!ctx) {
+        // No context is current on this thread yet: make the device's primary
+        // context current (cudaSetDevice initialises it; nothing is allocated).
+        if (cudaSetDevice(dev) != cudaSuccess) return KB_ERR_CUDA;
+        ctx = current_context();
+        if (!ctx) return KB_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_setup.find(ctx);
     if (it != g_setup.end() && it->second.device == dev) {

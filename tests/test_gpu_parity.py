@@ -243,7 +243,8 @@ def test_ragged_bad_messages_are_flagged_and_skipped(cuda_lib, oracle_mod):
 # -- Merkle trees ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n_leaves,leaf_bytes", [(1, 8), (2, 64), (3, 135), (5, 136), (7, 1001), (8, 8192),
                                                  (9, 7), (33, 200), (100, 64), (1000, 32), (64, 8192),
-                                                 (65, 16), (129, 8), (4097, 16), (10001, 8)])
+                                                 (65, 16), (129, 8), (4097, 16), (10001, 8), (32769, 8),
+                                                 (40001, 8), (98305, 8)])
 def test_merkle_levels_and_root(cuda_lib, oracle_mod, n_leaves, leaf_bytes):
     torch = _torch()
     buf = W.merkle_buffer(n_leaves, leaf_bytes, seed=n_leaves * 1000 + leaf_bytes)

@@ -11,6 +11,7 @@ from paper_1902_05320_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 THREADS = len(os.sched_getaffinity(0))
+RATES = (144, 136, 104, 72, 168, 136)
 
 
 def _dev(torch, a):
@@ -117,3 +118,58 @@ def test_fused_first_and_last_steps(cuda_lib, oracle_mod, seed, calls):
     cuda_lib.keccak_stream_absorb_final(states, d_msgs, _dev(torch, b.offsets), _dev(torch, b.lens),
                                         _dev(torch, b.out_lens), out, n)
     assert cuda_lib.keccak_last_error() != 0
+
+
+@pytest.mark.parametrize("seed", [321, 322])
+def test_stream_pieces_at_many_block_offsets(cuda_lib, oracle_mod, seed):
+    # Pieces are XORed into the lanes where they land, so the head of a piece
+    # starts at any byte of the open block and at any address alignment.
+    # Each call gives message i a piece of 0, 1, 2, 3 or 7 bytes, exactly the
+    # bytes that close its open block, one rate, one rate plus one byte, a
+    # random length below the rate, or all that is left; all six variants,
+    # messages at odd offsets.
+    import torch
+
+    rng = np.random.default_rng(seed)
+    n = 600
+    variants = (np.arange(n) % 6).astype(np.uint8)
+    rates = np.array(RATES, dtype=np.int64)[variants]
+    lens = rng.integers(0, 4 * rates + 9).astype(np.uint64)
+    offsets = np.zeros(n, dtype=np.uint64)
+    pos = 0
+    for i in range(n):
+        pos += int(rng.integers(1, 8))  # odd gaps: pieces start at every alignment
+        offsets[i] = pos
+        pos += int(lens[i])
+    msgs = W.random_bytes(pos + 8, seed=seed)
+    out_lens = np.where(variants < 4, np.array([28, 32, 48, 64, 0, 0])[variants],
+                        rng.integers(1, 400, size=n)).astype(np.uint32)
+    states = torch.zeros(n * cuda_lib.KB_STATE_BYTES, dtype=torch.uint8, device="cuda")
+    d_msgs = _dev(torch, msgs)
+    cuda_lib.keccak_stream_init(states, _dev(torch, variants), n)
+    cursor = np.zeros(n, dtype=np.uint64)
+    keep = []
+    heads = set()
+    calls = 0
+    while (cursor < lens).any():
+        remaining = (lens - cursor).astype(np.int64)
+        close = rates - (cursor.astype(np.int64) % rates)
+        choice = rng.integers(0, 10, size=n)
+        plen = np.select([choice < 5, choice == 5, choice == 6, choice == 7, choice == 8],
+                         [np.array([0, 1, 2, 3, 7])[np.minimum(choice, 4)], close, rates, rates + 1,
+                          rng.integers(1, rates)], remaining)
+        plen = np.minimum(plen, remaining).astype(np.uint64)
+        heads.update(zip(variants[plen > 0].tolist(), (cursor % rates.astype(np.uint64))[plen > 0].tolist()))
+        offs, pl = _dev(torch, offsets + cursor), _dev(torch, plen)
+        keep += [offs, pl]
+        cuda_lib.keccak_stream_absorb(states, d_msgs, offs, pl, n)
+        cursor += plen
+        calls += 1
+    assert calls > 5
+    assert len(heads) > 300  # distinct (variant, open-block offset) pairs a piece started at
+    out = torch.full((int(out_lens.sum()),), 0xEE, dtype=torch.uint8, device="cuda")
+    cuda_lib.keccak_stream_final(states, _dev(torch, out_lens), out, n)
+    torch.cuda.synchronize()
+    want = oracle_mod.hash_batch(msgs, offsets, lens, variants, out_lens, THREADS)
+    assert np.array_equal(out.cpu().numpy(), want)
+    assert cuda_lib.keccak_last_error() == 0
