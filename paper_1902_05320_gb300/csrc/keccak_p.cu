@@ -38,50 +38,63 @@ __host__ __device__ constexpr Rc255 make_rc255() {
 }
 static __constant__ Rc255 c_rc255 = make_rc255();
 
+// Widths up to 32: lane x + 5y in one 32-bit register that holds its w bits
+// 32/w times over (bit z of the lane at bits z, z + w, z + 2w, ...).  As 32 is
+// a multiple of w, rotating the register by n rotates every copy of the lane
+// by n within its w bits, so a lane rotation is one funnel shift with no
+// mask; XOR, AND and NOT keep the copies equal, and the round constant is
+// replicated the same way.  Only the low w bits are stored back.
 template <int W>
-__device__ __forceinline__ uint32_t rotw(uint32_t x, int n) {
-    constexpr uint32_t mask = W == 32 ? 0xffffffffu : ((1u << W) - 1u);
-    n %= W;
-    if (n == 0) return x;
-    return ((x << n) | (x >> (W - n))) & mask;
-}
+struct SmallLanes {
+    static constexpr uint32_t mask = W == 32 ? 0xffffffffu : ((1u << W) - 1u);
+    static constexpr uint32_t spread = 0xffffffffu / mask;  // 1 at bits 0, w, 2w, ...
+    __device__ static __forceinline__ uint32_t load(uint32_t v) { return (v & mask) * spread; }
+    __device__ static __forceinline__ uint32_t store(uint32_t v) { return v & mask; }
+    __device__ static __forceinline__ uint32_t rot(uint32_t x, int n) {
+        return n % W == 0 ? x : __funnelshift_l(x, x, uint32_t(n % W));
+    }
+};
 
-// Widths up to 32: one 32-bit word per lane.
 template <int W>
 __device__ __forceinline__ void small_round(uint32_t (&A)[25], int ir) {
+    using L = SmallLanes<W>;
     uint32_t C[5], D[5], Bv[25];
 #pragma unroll
     for (int x = 0; x < 5; ++x) C[x] = A[x] ^ A[x + 5] ^ A[x + 10] ^ A[x + 15] ^ A[x + 20];
 #pragma unroll
-    for (int x = 0; x < 5; ++x) D[x] = C[(x + 4) % 5] ^ rotw<W>(C[(x + 1) % 5], 1);
+    for (int x = 0; x < 5; ++x) D[x] = C[(x + 4) % 5] ^ L::rot(C[(x + 1) % 5], 1);
 #pragma unroll
     for (int y = 0; y < 5; ++y)
 #pragma unroll
         for (int x = 0; x < 5; ++x) {
             // pi: B[y, 2x+3y] takes rho(A[x, y])
             const int src = x + 5 * y;
-            Bv[y + 5 * ((2 * x + 3 * y) % 5)] = rotw<W>(A[src] ^ D[x], rho_offset(src));
+            Bv[y + 5 * ((2 * x + 3 * y) % 5)] = L::rot(A[src] ^ D[x], rho_offset(src));
         }
 #pragma unroll
     for (int y = 0; y < 5; ++y)
 #pragma unroll
         for (int x = 0; x < 5; ++x)
             A[x + 5 * y] = chi3(Bv[x + 5 * y], Bv[(x + 1) % 5 + 5 * y], Bv[(x + 2) % 5 + 5 * y]);
-    constexpr uint32_t mask = W == 32 ? 0xffffffffu : ((1u << W) - 1u);
-    A[0] ^= uint32_t(c_rc255.v[ir]) & mask;
+    A[0] ^= L::load(uint32_t(c_rc255.v[ir]));
 }
 
 // States move between global memory and registers through shared memory: a
 // block copies its tile of kThreads consecutive 200-byte states with
 // coalesced 8-byte accesses (a warp touches 256 contiguous bytes per access),
-// and each thread then reads its own state from shared memory.  Reading the
-// states straight from global memory, each thread 25 accesses 200 bytes
-// apart, left the reduced-round runs waiting on memory.
-constexpr uint32_t kTileWords = kThreads * 25;  // uint2 words of a tile (25.6 KB)
+// and each thread then reads its own state from shared memory.  Two tile
+// buffers: the next tile's copies (cp.async, 8 bytes each) are issued before
+// the current tile is permuted, so a block's loads overlap its own
+// arithmetic.  Reading the states straight from global memory, each thread
+// 25 accesses 200 bytes apart, left the reduced-round runs waiting on memory.
+constexpr uint32_t kTileWords = kThreads * 25;                     // uint2 words of a tile (25.6 KB)
+constexpr size_t kTileSmem = 2 * size_t(kTileWords) * sizeof(uint2);  // two buffers
 
-__device__ __forceinline__ void tile_in(uint2 *sm, const uint64_t *states, uint64_t first, uint32_t cnt) {
+__device__ __forceinline__ void tile_load_async(uint32_t sdst, const uint64_t *states, uint64_t first, uint32_t cnt) {
     const uint2 *src = reinterpret_cast<const uint2 *>(states + 25 * first);
-    for (uint32_t j = threadIdx.x; j < cnt * 25; j += kThreads) sm[j] = src[j];
+    for (uint32_t j = threadIdx.x; j < cnt * 25; j += kThreads)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sdst + 8 * j), "l"(src + j) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 __device__ __forceinline__ void tile_out(const uint2 *sm, uint64_t *states, uint64_t first, uint32_t cnt) {
@@ -89,34 +102,51 @@ __device__ __forceinline__ void tile_out(const uint2 *sm, uint64_t *states, uint
     for (uint32_t j = threadIdx.x; j < cnt * 25; j += kThreads) dst[j] = sm[j];
 }
 
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_keccak_p_small(uint64_t *states, int first_ir, int nr, uint64_t n) {
-    constexpr uint32_t mask = W == 32 ? 0xffffffffu : ((1u << W) - 1u);
-    __shared__ uint2 sm[kTileWords];
+// The tiles of blockIdx.x, gridDim.x apart, each permuted state by state by
+// f(uint2 *state) in shared memory and written back in place.
+template <class F>
+__device__ __forceinline__ void run_tiles(uint64_t *states, uint64_t n, uint2 *sm, F f) {
     const uint64_t ntiles = (n + kThreads - 1) / kThreads;
-    const int ir0 = ((first_ir % 255) + 255) % 255;  // rc has period 255 (Algorithm 5)
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t first = tile * kThreads;
-        const uint32_t cnt = uint32_t(n - first < kThreads ? n - first : uint64_t(kThreads));
-        tile_in(sm, states, first, cnt);
+    const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(sm));
+    auto count = [&](uint64_t t) { return uint32_t(n - t * kThreads < kThreads ? n - t * kThreads : uint64_t(kThreads)); };
+    uint64_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    tile_load_async(sbase, states, tile * kThreads, count(tile));
+    for (uint32_t b = 0; tile < ntiles; tile += gridDim.x, b ^= 1u) {
+        const uint64_t next = tile + gridDim.x;
+        // The other buffer was last read before the barrier that ended the
+        // previous pass, so the next tile may be copied into it now.
+        if (next < ntiles) tile_load_async(sbase + (b ^ 1u) * kTileWords * 8u, states, next * kThreads, count(next));
+        else asm volatile("cp.async.commit_group;" ::: "memory");  // an empty group keeps the count below uniform
+        asm volatile("cp.async.wait_group 1;" ::: "memory");         // this tile's copies have landed
         __syncthreads();
-        if (threadIdx.x < cnt) {
-            uint2 *s = sm + 25 * threadIdx.x;
-            uint32_t A[25];
-#pragma unroll
-            for (int k = 0; k < 25; ++k) A[k] = s[k].x & mask;
-            int ir = ir0;
-            for (int r = 0; r < nr; ++r) {
-                small_round<W>(A, ir);
-                ir = ir == 254 ? 0 : ir + 1;
-            }
-#pragma unroll
-            for (int k = 0; k < 25; ++k) s[k] = make_uint2(A[k], 0u);
-        }
+        uint2 *cur = sm + b * kTileWords;
+        const uint32_t cnt = count(tile);
+        if (threadIdx.x < cnt) f(cur + 25 * threadIdx.x);
         __syncthreads();
-        tile_out(sm, states, first, cnt);
+        tile_out(cur, states, tile * kThreads, cnt);
         __syncthreads();
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_keccak_p_small(uint64_t *states, int first_ir, int nr, uint64_t n) {
+    using L = SmallLanes<W>;
+    extern __shared__ uint2 sm[];
+    const int ir0 = ((first_ir % 255) + 255) % 255;  // rc has period 255 (Algorithm 5)
+    run_tiles(states, n, sm, [&](uint2 *s) {
+        uint32_t A[25];
+#pragma unroll
+        for (int k = 0; k < 25; ++k) A[k] = L::load(s[k].x);
+        int ir = ir0;
+        for (int r = 0; r < nr; ++r) {
+            small_round<W>(A, ir);
+            ir = ir == 254 ? 0 : ir + 1;
+        }
+#pragma unroll
+        for (int k = 0; k < 25; ++k) s[k] = make_uint2(L::store(A[k]), 0u);
+    });
 }
 
 // One round of Keccak-p[1600] (Eq. 10) with round-constant index ir of the
@@ -166,30 +196,19 @@ __device__ __forceinline__ void p1600_rounds(uint32_t (&L)[25], uint32_t (&H)[25
 template <bool STAGED>
 __global__ void __launch_bounds__(kThreads) k_keccak_p_1600(uint64_t *states, int first_ir, int nr, uint64_t n) {
     if constexpr (STAGED) {
-        __shared__ uint2 sm[kTileWords];
-        const uint64_t ntiles = (n + kThreads - 1) / kThreads;
-        for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const uint64_t first = tile * kThreads;
-            const uint32_t cnt = uint32_t(n - first < kThreads ? n - first : uint64_t(kThreads));
-            tile_in(sm, states, first, cnt);
-            __syncthreads();
-            if (threadIdx.x < cnt) {
-                uint2 *s = sm + 25 * threadIdx.x;
-                uint32_t L[25], H[25];
+        extern __shared__ uint2 sm[];
+        run_tiles(states, n, sm, [&](uint2 *s) {
+            uint32_t L[25], H[25];
 #pragma unroll
-                for (int k = 0; k < 25; ++k) {
-                    const uint2 v = s[k];
-                    L[k] = v.x;
-                    H[k] = v.y;
-                }
-                p1600_rounds(L, H, first_ir, nr);
-#pragma unroll
-                for (int k = 0; k < 25; ++k) s[k] = make_uint2(L[k], H[k]);
+            for (int k = 0; k < 25; ++k) {
+                const uint2 v = s[k];
+                L[k] = v.x;
+                H[k] = v.y;
             }
-            __syncthreads();
-            tile_out(sm, states, first, cnt);
-            __syncthreads();
-        }
+            p1600_rounds(L, H, first_ir, nr);
+#pragma unroll
+            for (int k = 0; k < 25; ++k) s[k] = make_uint2(L[k], H[k]);
+        });
     } else {
         const uint64_t step = uint64_t(gridDim.x) * blockDim.x;
         for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += step) {
@@ -208,11 +227,21 @@ __global__ void __launch_bounds__(kThreads) k_keccak_p_1600(uint64_t *states, in
     }
 }
 
+// Launches a tiled kernel with its two tile buffers (above the 48 KB a block
+// gets without opting in).
+template <class K>
+int launch_tiled(K kernel, uint64_t *states, int first_ir, int nr, uint64_t n, cudaStream_t stream,
+                 const DeviceInfo &dev) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTileSmem)) != cudaSuccess)
+        return cuda_status(cudaGetLastError());
+    const uint64_t g = persistent_grid(reinterpret_cast<const void *>(kernel), kThreads, kTileSmem, n, dev);
+    kernel<<<unsigned(g), kThreads, kTileSmem, stream>>>(states, first_ir, nr, n);
+    return cuda_status(cudaGetLastError());
+}
+
 template <int W>
 int launch_small(uint64_t *states, int first_ir, int nr, uint64_t n, cudaStream_t stream, const DeviceInfo &dev) {
-    const uint64_t g = persistent_grid(reinterpret_cast<const void *>(&k_keccak_p_small<W>), kThreads, 0, n, dev);
-    k_keccak_p_small<W><<<unsigned(g), kThreads, 0, stream>>>(states, first_ir, nr, n);
-    return cuda_status(cudaGetLastError());
+    return launch_tiled(k_keccak_p_small<W>, states, first_ir, nr, n, stream, dev);
 }
 
 }  // namespace
@@ -233,15 +262,10 @@ int launch_keccak_p(uint64_t *states, int b, int nr, uint64_t n, cudaStream_t st
         default: {
             // Staged through shared memory below 16 rounds (measured: 12
             // rounds 2.53 -> 2.35 ms on 2^24 states; 24 rounds 3.84 -> 4.19 ms).
-            if (nr < 16) {
-                const uint64_t g =
-                    persistent_grid(reinterpret_cast<const void *>(&k_keccak_p_1600<true>), kThreads, 0, n, dev);
-                k_keccak_p_1600<true><<<unsigned(g), kThreads, 0, stream>>>(states, first_ir, nr, n);
-            } else {
-                const uint64_t g =
-                    persistent_grid(reinterpret_cast<const void *>(&k_keccak_p_1600<false>), kThreads, 0, n, dev);
-                k_keccak_p_1600<false><<<unsigned(g), kThreads, 0, stream>>>(states, first_ir, nr, n);
-            }
+            if (nr < 16) return launch_tiled(k_keccak_p_1600<true>, states, first_ir, nr, n, stream, dev);
+            const uint64_t g =
+                persistent_grid(reinterpret_cast<const void *>(&k_keccak_p_1600<false>), kThreads, 0, n, dev);
+            k_keccak_p_1600<false><<<unsigned(g), kThreads, 0, stream>>>(states, first_ir, nr, n);
             return cuda_status(cudaGetLastError());
         }
     }

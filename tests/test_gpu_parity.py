@@ -652,6 +652,28 @@ def test_keccak_p_several_tiles(cuda_lib, oracle_mod, b, nr):
         assert np.array_equal(_lanes_to_bits(got[i], w), want), (b, nr, i)
 
 
+@pytest.mark.parametrize("b,nr", [(200, 18), (1600, 12), (25, 7), (800, 22)])
+def test_keccak_p_many_tiles_per_block(cuda_lib, oracle_mod, b, nr):
+    # Enough states that every block of the persistent grid runs several
+    # tiles (its next tile's copies in flight while it permutes the current
+    # one), with a partial last tile; sampled states against the oracle, the
+    # states after the n given ones untouched.
+    torch = _torch()
+    w = b // 25
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n, extra = 128 * 8 * sms * 3 + 77, 3
+    rng = np.random.default_rng(b * 7 + nr)
+    states = rng.integers(0, 2**64, size=(n + extra, 25), dtype=np.uint64) & np.uint64((1 << w) - 1)
+    d = torch.from_numpy(states.view(np.int64).copy()).cuda()
+    cuda_lib.keccak_p_batch(d, b, nr, n)
+    got = d.cpu().numpy().view(np.uint64).reshape(n + extra, 25)
+    assert np.array_equal(got[n:], states[n:])
+    sample = list(rng.choice(n, 150, replace=False)) + [0, 127, 128, n - 78, n - 77, n - 1]
+    for i in sample:
+        want = oracle_mod.keccak_p(b, nr, _lanes_to_bits(states[i], w))
+        assert np.array_equal(_lanes_to_bits(got[i], w), want), (b, nr, i)
+
+
 @pytest.mark.parametrize("b", [25, 50, 100, 200, 400, 800, 1600])
 def test_keccak_p_every_width_and_round_count(cuda_lib, oracle_mod, b):
     torch = _torch()
