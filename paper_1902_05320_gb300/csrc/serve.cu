@@ -13,7 +13,11 @@
 //      posts the request id to a completion ring in host memory (system-scope
 //      atomic), so a short request completes as soon as its own hash does,
 //      not when the longest message of its batch does;
-//   4. an event marks the batch done; its arena region and slot are reused.
+//   4. an event marks the batch done; its stream slot is reused.  A
+//      short-lane batch holds one arena region until then; in the long lane
+//      each request has its own region, given back as soon as its
+//      completion arrives, so a finished request's bytes do not wait for the
+//      longest chain of its batch.
 // Host threads: the caller submits; a dispatcher forms and launches batches;
 // a completer drains the completion ring and retires finished batches.  If
 // the device lacks native host atomics, requests complete with their batch.
@@ -141,7 +145,10 @@ struct Request {
     uint8_t variant = 0;
     int64_t t_arrive = 0;              // ns since the server started
     std::atomic<int64_t> t_done{-1};   // ns since the server started, -1 while pending
+    uint64_t region = ~uint64_t(0);    // its own arena region in the long lane (under the lock); none: ~0
 };
+
+constexpr uint64_t kNoRegion = ~uint64_t(0);
 
 // Request table: fixed array of chunk pointers, so readers need no lock.
 constexpr uint32_t kChunk = 1u << 16;
@@ -156,6 +163,7 @@ struct Slot {
     uint64_t region_start = 0, region_bytes = 0;
     bool busy = false;      // holds a batch (set by the dispatcher under the lock)
     bool launched = false;  // its completion event has been recorded
+    bool per_request = false;  // each request has its own arena region (Request::region)
 };
 
 uint64_t align16(uint64_t v) { return (v + 15) & ~uint64_t(15); }
@@ -242,9 +250,31 @@ struct Server {
     }
 
     // Forms one batch into slot s from the lane's pending queue (lock held).
-    bool form_batch(Lane &ln, Slot &s) {
+    // per_request: each request takes its own region of the lane's arena, in
+    // arrival order while one fits, and gives it back as soon as its own
+    // completion arrives (see complete_loop); otherwise the batch takes one
+    // region, given back when the whole batch is done.
+    bool form_batch(Lane &ln, Slot &s, bool per_request) {
         s.ids.clear();
+        s.per_request = per_request;
         uint64_t bytes = 0;
+        if (per_request) {
+            for (uint32_t id : ln.pending) {
+                Request &r = req(id);
+                const uint64_t need = align16(r.len);
+                if (s.ids.size() >= cfg.max_batch_requests || bytes + need > cfg.max_batch_bytes) break;
+                uint64_t start = 0;
+                if (!ln.heap.alloc(std::max<uint64_t>(need, 16), &start)) break;
+                r.region = start;
+                s.ids.push_back(id);
+                bytes += need;
+            }
+            if (s.ids.empty()) return false;
+            ln.pending.erase(ln.pending.begin(), ln.pending.begin() + s.ids.size());
+            s.region_start = ln.base;
+            s.region_bytes = 0;
+            return true;
+        }
         for (uint32_t id : ln.pending) {
             const Request &r = req(id);
             const uint64_t need = align16(r.len);
@@ -282,7 +312,8 @@ struct Server {
             ReqDesc &dsc = s.h_desc[k];
             dsc.src = reinterpret_cast<uint64_t>(r.msg);
             dsc.len = r.len;
-            dsc.arena_off = off;
+            // (region_start is the lane's base for per-request regions)
+            dsc.arena_off = s.per_request ? s.region_start + r.region : off;
             dsc.out = reinterpret_cast<uint64_t>(r.out);
             dsc.chunk_base = chunks;
             dsc.out_len = r.out_len;
@@ -324,7 +355,7 @@ struct Server {
                         slot = &sl;
                         break;
                     }
-                if (!slot || !form_batch(ln, *slot)) continue;
+                if (!slot || !form_batch(ln, *slot, li == kLongLane && ring_mode)) continue;
                 slot->busy = true;
                 slot->launched = false;
                 ++batches;
@@ -348,10 +379,20 @@ struct Server {
         }
     }
 
+    // Gives back the arena region of a request that has its own (lock held).
+    void release_region(uint32_t id) {
+        Request &r = req(id);
+        if (r.region == kNoRegion) return;
+        lanes[kLongLane].heap.free(r.region);
+        r.region = kNoRegion;
+    }
+
     void complete_loop() {
         cudaSetDevice(device);
+        std::vector<uint32_t> finished;  // completed this pass, in ring order
         while (true) {
             bool progress = false;
+            finished.clear();
             if (ring_mode) {
                 volatile unsigned long long *prod = &ring->produced;
                 const unsigned long long p = *prod;
@@ -363,12 +404,17 @@ struct Server {
                     if (v == 0) break;  // written late; pick it up next pass
                     *slot = 0;
                     complete(v - 1, now_ns());
+                    finished.push_back(v - 1);
                     ++consumed;
                     progress = true;
                 }
             }
             {
                 std::lock_guard<std::mutex> lk(mu);
+                // A finished request's own region can take new messages at
+                // once: its hashing has read them (the ring entry is posted
+                // after the sponge), whatever the rest of its batch is doing.
+                for (uint32_t id : finished) release_region(id);
                 for (Lane &ln : lanes)
                 for (auto &s : ln.slots) {
                     if (!s.busy || !s.launched) continue;
@@ -380,7 +426,11 @@ struct Server {
                         if (!ring_mode) complete(id, t);
                         bytes_done += req(id).len;
                     }
-                    ln.heap.free(s.region_start - ln.base);
+                    if (s.per_request) {
+                        for (uint32_t id : s.ids) release_region(id);  // any whose entry is not read yet
+                    } else {
+                        ln.heap.free(s.region_start - ln.base);
+                    }
                     s.busy = false;
                     progress = true;
                 }
