@@ -975,6 +975,8 @@ def serving_measurements(workloads, torch, rank, rate=200_000, seconds=10.0, wit
            "p50_us_small_lt_4KiB": float(np.percentile(lat[wl.lens < 4096], 50) / 1e3),
            "p99_us_small_lt_4KiB": float(np.percentile(lat[wl.lens < 4096], 99) / 1e3),
            "p50_us_large_ge_512KiB": float(np.percentile(lat[big], 50) / 1e3) if big.any() else None,
+           "latency_parts_us": {k: st[k] for k in ("submit_lag_p50_us", "submit_lag_p99_us", "queue_wait_p50_us",
+                                                    "queue_wait_p99_us", "service_p50_us", "service_p99_us")},
            "pool_numa_node": pool_node, "outputs_numa_node": out_node, "clocks": sampler.summary()}
     if with_oracle:
         import oracle

@@ -397,6 +397,14 @@ typedef struct {
     double wall_s;                    /* first arrival to last completion */
     double throughput_rps, throughput_gbs;
     double lat_mean_us, lat_p50_us, lat_p90_us, lat_p99_us, lat_p999_us, lat_max_us;
+    /* Where a request's latency went (p50 and p99 over the replay's requests):
+     * submit lag = when the replay handed it to the server minus its
+     * scheduled arrival (host side); queue wait = batch launch minus submit
+     * (waiting for a stream slot or arena space); service = completion minus
+     * batch launch (copy into the arena, hashing, completion). */
+    double submit_lag_p50_us, submit_lag_p99_us;
+    double queue_wait_p50_us, queue_wait_p99_us;
+    double service_p50_us, service_p99_us;
 } kb_server_stats;
 
 /* Creates a server on the current device; NULL on error (*status says why:

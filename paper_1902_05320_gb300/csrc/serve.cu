@@ -144,6 +144,8 @@ struct Request {
     uint32_t out_len = 0;
     uint8_t variant = 0;
     int64_t t_arrive = 0;              // ns since the server started
+    int64_t t_submit = 0;              // when submit() took it
+    std::atomic<int64_t> t_launch{-1}; // when its batch was enqueued
     std::atomic<int64_t> t_done{-1};   // ns since the server started, -1 while pending
     uint64_t region = ~uint64_t(0);    // its own arena region in the long lane (under the lock); none: ~0
 };
@@ -198,16 +200,24 @@ struct Server {
     uint64_t long_threshold = 64;     // cost (permutations) above which a request is long
     bool long_lanes_kernel = true;    // long lane: one warp per request
     Lane lanes[2];
-    std::mutex mu;                    // pending queues, slots, arena heaps, stats
+    // Two locks, so that submitting never waits for batch formation: qmu
+    // guards only the lanes' pending queues (submit pushes at the back, the
+    // dispatcher alone takes from the front); mu guards the slots, the arena
+    // heaps, Request::region and the stats.  Order: mu before qmu.
+    std::mutex mu;
+    std::mutex qmu;
+    std::mutex chunk_mu;              // creation of request-table chunks
     std::condition_variable cv;
     std::unique_ptr<Request[]> chunks[kMaxChunks];
     std::atomic<uint32_t> n_requests{0};
     std::atomic<uint64_t> n_done{0};
     std::atomic<bool> stop{false};
     std::atomic<int> error{KB_OK};
-    uint64_t batches = 0, max_batch_seen = 0, bytes_done = 0, rejected = 0;
+    uint64_t batches = 0, max_batch_seen = 0, bytes_done = 0;
+    std::atomic<uint64_t> rejected{0};
     Clock::time_point t0;
     std::thread dispatcher, completer;
+    std::vector<uint32_t> candidates;  // the dispatcher's copy of a lane's oldest pending ids
 
     Request &req(uint32_t id) { return chunks[id / kChunk][id % kChunk]; }
     int64_t now_ns() const {
@@ -222,14 +232,13 @@ struct Server {
         if ((len && !msg) || (out_len && !out) || out_len > (1u << 20)) return KB_ERR_INVALID;
         const int lane = request_cost(len, variant, out_len) > long_threshold ? kLongLane : kShortLane;
         if (align16(len) > lanes[lane].max_len || align16(len) > cfg.max_batch_bytes) {
-            std::lock_guard<std::mutex> lk(mu);
-            ++rejected;
+            rejected.fetch_add(1);
             return KB_ERR_TOO_LARGE;
         }
         const uint32_t id = n_requests.fetch_add(1);
         if (id / kChunk >= kMaxChunks) return KB_ERR_NOMEM;
         {
-            std::lock_guard<std::mutex> lk(mu);
+            std::lock_guard<std::mutex> lk(chunk_mu);
             if (!chunks[id / kChunk]) chunks[id / kChunk].reset(new Request[kChunk]);
         }
         Request &r = req(id);
@@ -238,10 +247,12 @@ struct Server {
         r.out = out;
         r.out_len = out_len;
         r.variant = uint8_t(variant);
-        r.t_arrive = t_arrive >= 0 ? t_arrive : now_ns();
+        r.t_submit = now_ns();
+        r.t_arrive = t_arrive >= 0 ? t_arrive : r.t_submit;
+        r.t_launch.store(-1, std::memory_order_relaxed);
         r.t_done.store(-1);
         {
-            std::lock_guard<std::mutex> lk(mu);
+            std::lock_guard<std::mutex> lk(qmu);
             lanes[lane].pending.push_back(id);
         }
         cv.notify_all();
@@ -249,7 +260,14 @@ struct Server {
         return KB_OK;
     }
 
-    // Forms one batch into slot s from the lane's pending queue (lock held).
+    bool has_pending(const Lane &ln) {
+        std::lock_guard<std::mutex> q(qmu);
+        return !ln.pending.empty();
+    }
+
+    // Forms one batch into slot s from the lane's pending queue (mu held; qmu
+    // is taken only to copy the oldest candidates and, at the end, to drop
+    // the admitted ones from the front, which no other thread removes).
     // per_request: each request takes its own region of the lane's arena, in
     // arrival order while one fits, and gives it back as soon as its own
     // completion arrives (see complete_loop); otherwise the batch takes one
@@ -257,9 +275,19 @@ struct Server {
     bool form_batch(Lane &ln, Slot &s, bool per_request) {
         s.ids.clear();
         s.per_request = per_request;
+        std::vector<uint32_t> &cand = candidates;
+        {
+            std::lock_guard<std::mutex> q(qmu);
+            const size_t k = std::min<size_t>(ln.pending.size(), cfg.max_batch_requests);
+            cand.assign(ln.pending.begin(), ln.pending.begin() + k);
+        }
+        auto pop_admitted = [&] {
+            std::lock_guard<std::mutex> q(qmu);
+            ln.pending.erase(ln.pending.begin(), ln.pending.begin() + s.ids.size());
+        };
         uint64_t bytes = 0;
         if (per_request) {
-            for (uint32_t id : ln.pending) {
+            for (uint32_t id : cand) {
                 Request &r = req(id);
                 const uint64_t need = align16(r.len);
                 if (s.ids.size() >= cfg.max_batch_requests || bytes + need > cfg.max_batch_bytes) break;
@@ -270,12 +298,12 @@ struct Server {
                 bytes += need;
             }
             if (s.ids.empty()) return false;
-            ln.pending.erase(ln.pending.begin(), ln.pending.begin() + s.ids.size());
+            pop_admitted();
             s.region_start = ln.base;
             s.region_bytes = 0;
             return true;
         }
-        for (uint32_t id : ln.pending) {
+        for (uint32_t id : cand) {
             const Request &r = req(id);
             const uint64_t need = align16(r.len);
             if (s.ids.size() >= cfg.max_batch_requests || bytes + need > cfg.max_batch_bytes) break;
@@ -291,7 +319,7 @@ struct Server {
             s.ids.pop_back();
         }
         if (s.ids.empty()) return false;
-        ln.pending.erase(ln.pending.begin(), ln.pending.begin() + s.ids.size());
+        pop_admitted();
         s.region_start = ln.base + start;
         s.region_bytes = std::max<uint64_t>(bytes, 16);
         return true;
@@ -307,8 +335,10 @@ struct Server {
             return request_cost(x.len, x.variant, x.out_len) > request_cost(y.len, y.variant, y.out_len);
         });
         uint64_t off = s.region_start, chunks = 0;
+        const int64_t t_launch = now_ns();
         for (size_t k = 0; k < s.ids.size(); ++k) {
-            const Request &r = req(s.ids[k]);
+            Request &r = req(s.ids[k]);
+            r.t_launch.store(t_launch, std::memory_order_relaxed);
             ReqDesc &dsc = s.h_desc[k];
             dsc.src = reinterpret_cast<uint64_t>(r.msg);
             dsc.len = r.len;
@@ -348,7 +378,7 @@ struct Server {
             bool launched_any = false;
             for (int li = 0; li < 2; ++li) {
                 Lane &ln = lanes[li];
-                if (ln.pending.empty()) continue;
+                if (!has_pending(ln)) continue;
                 Slot *slot = nullptr;
                 for (auto &sl : ln.slots)
                     if (!sl.busy) {
@@ -644,11 +674,28 @@ int kb_server_replay(kb_server *handle, const uint8_t *pool, const uint64_t *off
         stats->lat_p99_us = pct(0.99);
         stats->lat_p999_us = pct(0.999);
         stats->lat_max_us = double(sorted[n - 1]) / 1e3;
+        // The latency's parts: submit lag, queue wait, service.
+        std::vector<int64_t> part(n);
+        auto pct_of = [&](auto get, double q) {
+            for (uint64_t i = 0; i < n; ++i) part[i] = get(s->req(uint32_t(first + i)));
+            const size_t k = std::min<size_t>(n - 1, size_t(q * double(n)));
+            std::nth_element(part.begin(), part.begin() + k, part.end());
+            return double(part[k]) / 1e3;
+        };
+        auto lag = [](const Request &r) { return r.t_submit - r.t_arrive; };
+        auto wait = [](const Request &r) { return r.t_launch.load(std::memory_order_relaxed) - r.t_submit; };
+        auto service = [](const Request &r) { return r.t_done.load() - r.t_launch.load(std::memory_order_relaxed); };
+        stats->submit_lag_p50_us = pct_of(lag, 0.50);
+        stats->submit_lag_p99_us = pct_of(lag, 0.99);
+        stats->queue_wait_p50_us = pct_of(wait, 0.50);
+        stats->queue_wait_p99_us = pct_of(wait, 0.99);
+        stats->service_p50_us = pct_of(service, 0.50);
+        stats->service_p99_us = pct_of(service, 0.99);
         std::lock_guard<std::mutex> lk(s->mu);
         stats->batches = s->batches;
         stats->max_batch_requests_seen = s->max_batch_seen;
         stats->peak_arena_bytes = s->lanes[0].heap.peak() + s->lanes[1].heap.peak();
-        stats->rejected = s->rejected;
+        stats->rejected = s->rejected.load();
         stats->completion_ring = s->ring_mode ? 1 : 0;
     }
     return KB_OK;

@@ -27,7 +27,10 @@ class ServerStats(ctypes.Structure):
                 ("wall_s", ctypes.c_double), ("throughput_rps", ctypes.c_double),
                 ("throughput_gbs", ctypes.c_double), ("lat_mean_us", ctypes.c_double),
                 ("lat_p50_us", ctypes.c_double), ("lat_p90_us", ctypes.c_double), ("lat_p99_us", ctypes.c_double),
-                ("lat_p999_us", ctypes.c_double), ("lat_max_us", ctypes.c_double)]
+                ("lat_p999_us", ctypes.c_double), ("lat_max_us", ctypes.c_double),
+                ("submit_lag_p50_us", ctypes.c_double), ("submit_lag_p99_us", ctypes.c_double),
+                ("queue_wait_p50_us", ctypes.c_double), ("queue_wait_p99_us", ctypes.c_double),
+                ("service_p50_us", ctypes.c_double), ("service_p99_us", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}

@@ -43,6 +43,11 @@ def test_server_replay_matches_oracle(cuda_lib, oracle_mod, long_lane_parallel):
         got, lat, stats, _ = _replay(srv, torch, wl)
     assert stats["requests"] == wl.n and (lat > 0).all()
     assert stats["lat_p50_us"] <= stats["lat_p99_us"] <= stats["lat_max_us"]
+    # The latency's parts: each request is submitted no earlier than its
+    # arrival, launched after it is submitted and completed after its launch.
+    assert 0 <= stats["submit_lag_p50_us"] <= stats["submit_lag_p99_us"] <= stats["lat_max_us"]
+    assert 0 <= stats["queue_wait_p50_us"] <= stats["queue_wait_p99_us"] <= stats["lat_max_us"]
+    assert 0 < stats["service_p50_us"] <= stats["service_p99_us"] <= stats["lat_max_us"]
     want = oracle_mod.hash_batch(wl.pool, wl.offsets, wl.lens, wl.variants, wl.out_lens, THREADS)
     assert np.array_equal(got, want)
 
