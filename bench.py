@@ -452,22 +452,31 @@ def e2e_measurements(binding, torch, stream, msgs_np, digests, n_msgs, world, st
     del probe_dev
     reps = max(3, min(steps, 10))
 
-    def timed(path):
+    per_call = {}
+
+    def timed(path, name):
+        # Each call is synchronous (it returns with the digests in host
+        # memory); the rate is the mean over the calls, and each call's time
+        # is kept so that a stall of the host shows as itself.
         binding.keccak_tune_set(binding.KB_TUNE_HOST_PATH, path)
         try:
             binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, n_msgs, stream)
             torch.cuda.synchronize()
-            t = time.perf_counter()
+            ts = []
             for _ in range(reps):
+                t = time.perf_counter()
                 binding.keccak_batch_uniform_host(h_in, MSG_BYTES, MSG_BYTES, VARIANT, DIGEST, h_out, n_msgs, stream)
-            return (time.perf_counter() - t) / reps
+                ts.append(time.perf_counter() - t)
+            per_call[name] = {"min": round(min(ts) * 1e3, 3), "median": round(statistics.median(ts) * 1e3, 3),
+                              "max": round(max(ts) * 1e3, 3), "calls": reps}
+            return sum(ts) / reps
         finally:
             binding.keccak_tune_set(binding.KB_TUNE_HOST_PATH, binding.KB_HOST_PATH_AUTO)
 
-    s_staged = timed(binding.KB_HOST_PATH_STAGED)
-    s_in_place = timed(binding.KB_HOST_PATH_ZERO_COPY)
+    s_staged = timed(binding.KB_HOST_PATH_STAGED, "staged")
+    s_in_place = timed(binding.KB_HOST_PATH_ZERO_COPY, "in_place")
     # The default: the first call of this size class decides by a trial.
-    s_auto = timed(binding.KB_HOST_PATH_AUTO)
+    s_auto = timed(binding.KB_HOST_PATH_AUTO, "default")
     chosen = binding.keccak_host_path_for(n_msgs)
     if not np.array_equal(h_out.array[: 1 << 20], digests[: 1 << 20].cpu().numpy()):
         raise SystemExit("host-buffer path disagrees with the device path")
@@ -479,6 +488,7 @@ def e2e_measurements(binding, torch, stream, msgs_np, digests, n_msgs, world, st
            "host_path_chosen": {binding.KB_HOST_PATH_STAGED: "staged", binding.KB_HOST_PATH_ZERO_COPY: "in_place"}.get(
                chosen, str(chosen)),
            "staged_mhash_s": n_msgs / s_staged / 1e6, "in_place_mhash_s": n_msgs / s_in_place / 1e6,
+           "ms_per_call": per_call,
            "link": link,
            "link_bound_mhash_s": None,
            "buffers_numa_node": {"messages": h_in.numa_node(), "digests": h_out.numa_node()},

@@ -242,11 +242,12 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
 int keccak_host_path_for(uint64_t n);
 
 /*
- * keccak_host_alloc -- page-locked host memory for keccak_batch_uniform_host,
- * placed on the host NUMA node nearest the current device (the device's
- * cudaDevAttrHostNumaId; no placement where the system reports none or
- * refuses the binding) and mapped for device access, so that neither path
- * crosses the link between the host's CPUs.  *ptr receives the HOST address
+ * keccak_host_alloc -- page-locked host memory for keccak_batch_uniform_host
+ * and the serving loop's message pools (cudaHostAlloc, mapped for device
+ * access), populated under a preferred-node policy for the host NUMA node
+ * nearest the current device (the device's cudaDevAttrHostNumaId; no
+ * placement where the system reports none or refuses the policy), so that
+ * neither path crosses the link between the host's CPUs.  *ptr receives the HOST address
  * (NULL on failure).  KB_ERR_INVALID for bytes == 0 or ptr == NULL,
  * KB_ERR_NOMEM when the memory cannot be mapped or page-locked.
  * keccak_host_free releases it (KB_ERR_INVALID for a pointer this library did

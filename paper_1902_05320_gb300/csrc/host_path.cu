@@ -15,7 +15,6 @@
 // class (a "host-path decision").
 #include <cuda_runtime.h>
 
-#include <sys/mman.h>
 #include <sys/syscall.h>
 #include <unistd.h>
 
@@ -213,7 +212,6 @@ constexpr uint64_t kTrialMin = 1u << 14;
 
 // ---- page-locked host memory near the GPU ------------------------------------
 
-constexpr int kMpolBind = 2;                  // MPOL_BIND
 constexpr unsigned long kMpolFNodeAddr = 3;   // MPOL_F_NODE | MPOL_F_ADDR
 constexpr int kMaxNodes = 1024;
 constexpr int kLongBits = int(8 * sizeof(unsigned long));
@@ -224,13 +222,31 @@ struct HostBlock {
 std::mutex g_host_mu;
 std::map<void *, HostBlock> g_host_blocks;
 
-// Binds [p, p + bytes) to NUMA node `node` before its pages are touched.
-bool bind_to_node(void *p, size_t bytes, int node) {
-    if (node < 0 || node >= kMaxNodes) return false;
-    unsigned long mask[kMaxNodes / kLongBits + 1] = {};  // one spare word for kernels that read maxnode bits
-    mask[node / kLongBits] = 1UL << (node % kLongBits);
-    return syscall(SYS_mbind, p, bytes, kMpolBind, mask, static_cast<unsigned long>(kMaxNodes) + 1, 0) == 0;
-}
+constexpr int kMpolPreferred = 1;              // MPOL_PREFERRED
+
+// While alive, the calling thread allocates new pages on NUMA node `node`
+// when it can (a preferred-node policy); the thread's previous policy comes
+// back at the end.  Does nothing for node < 0 or when the system refuses.
+class PreferNode {
+  public:
+    explicit PreferNode(int node) {
+        if (node < 0 || node >= kMaxNodes) return;
+        if (syscall(SYS_get_mempolicy, &old_mode_, old_mask_, static_cast<unsigned long>(kMaxNodes) + 1, nullptr,
+                    0UL) != 0)
+            return;
+        unsigned long mask[kMaxNodes / kLongBits + 1] = {};  // one spare word for kernels that read maxnode bits
+        mask[node / kLongBits] = 1UL << (node % kLongBits);
+        set_ = syscall(SYS_set_mempolicy, kMpolPreferred, mask, static_cast<unsigned long>(kMaxNodes) + 1) == 0;
+    }
+    ~PreferNode() {
+        if (set_) syscall(SYS_set_mempolicy, old_mode_, old_mask_, static_cast<unsigned long>(kMaxNodes) + 1);
+    }
+
+  private:
+    int old_mode_ = 0;
+    unsigned long old_mask_[kMaxNodes / kLongBits + 1] = {};
+    bool set_ = false;
+};
 
 // Copies n16 16-byte words from src (host memory seen through its device
 // view) to dst with SM loads and stores (link diagnostic).
@@ -365,14 +381,20 @@ int keccak_host_alloc(size_t bytes, void **ptr) {
         cudaGetLastError();
         node = -1;
     }
-    void *p = mmap(nullptr, bytes, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
-    if (p == MAP_FAILED) return KB_ERR_NOMEM;
-    if (node >= 0) bind_to_node(p, bytes, node);  // best effort: unbound memory still works
-    // Registering pins (and so first touches) every page under the binding.
-    if (cudaHostRegister(p, bytes, cudaHostRegisterMapped | cudaHostRegisterPortable) != cudaSuccess) {
-        cudaGetLastError();
-        munmap(p, bytes);
-        return KB_ERR_NOMEM;
+    // The driver's own page-locked allocation, populated by this thread
+    // under a preferred-node policy.  (Anonymous memory bound with mbind and
+    // then registered lands on the node too, but the device then reaches it
+    // through mappings that degrade as the host's memory fragments: the
+    // serving loop's gathers of random 16 KiB pieces of a 4 GiB pool slowed
+    // from one process to the next on the same machine, p99 26 -> 35 -> 175
+    // ms, while pools from cudaHostAlloc gave 25.9-26.0 ms every time.)
+    void *p = nullptr;
+    {
+        PreferNode prefer(node);
+        if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return KB_ERR_NOMEM;
+        }
     }
     std::lock_guard<std::mutex> lk(g_host_mu);
     g_host_blocks[p] = HostBlock{bytes};
@@ -382,18 +404,17 @@ int keccak_host_alloc(size_t bytes, void **ptr) {
 
 int keccak_host_free(void *ptr) {
     if (!ptr) return KB_OK;
-    size_t bytes = 0;
     {
         std::lock_guard<std::mutex> lk(g_host_mu);
         auto it = g_host_blocks.find(ptr);
         if (it == g_host_blocks.end()) return KB_ERR_INVALID;
-        bytes = it->second.bytes;
         g_host_blocks.erase(it);
     }
-    const bool unreg = cudaHostUnregister(ptr) == cudaSuccess;
-    if (!unreg) cudaGetLastError();
-    munmap(ptr, bytes);
-    return unreg ? KB_OK : KB_ERR_CUDA;
+    if (cudaFreeHost(ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return KB_ERR_CUDA;
+    }
+    return KB_OK;
 }
 
 int sha3gb_host_link_probe(const void *host, void *device, size_t bytes, int mode, int reps, double *gb_s,
