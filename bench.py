@@ -248,6 +248,8 @@ def main() -> None:
                     help="only run the Merkle measurement on LEAVES 8 KiB leaves (profiling captures)")
     ap.add_argument("--ragged-only", type=int, default=0, metavar="N",
                     help="only run the ragged-batch measurement on N messages (profiling captures)")
+    ap.add_argument("--keccak-p-only", default="", metavar="B,NR,N",
+                    help="only time Keccak-p[B, NR] on N raw states (profiling captures)")
     ap.add_argument("--next-only", action="store_true",
                     help="only run the streaming, many-tree, message-tree and Keccak-p measurements")
     ap.add_argument("--config", type=int, default=0, choices=sorted(CONFIG_WORKLOADS),
@@ -286,6 +288,9 @@ def main() -> None:
         return
     if args.config:
         print(json.dumps(config_measurement(args.config, binding, workloads, torch, rank)), flush=True)
+        return
+    if args.keccak_p_only:
+        print(json.dumps(keccak_p_measurement(binding, workloads, torch, rank, args.keccak_p_only)), flush=True)
         return
     if args.next_only:
         print(json.dumps(next_rows_measurements(binding, workloads, torch, torch.cuda.current_stream(), rank)),
@@ -1000,6 +1005,26 @@ def serving_measurements(workloads, torch, rank, rate=200_000, seconds=10.0, wit
         e["capacity_rps_extrapolated"] = wl.n / (e["full_ms_extrapolated"] / 1e3)
         res["oracle"] = e
     return res
+
+
+def keccak_p_measurement(binding, workloads, torch, rank, spec: str) -> dict:
+    """Keccak-p[b, n_r] in place on n random 200-byte states: the median of
+    five launches after three warm-up launches."""
+    b, nr, n = (int(x) for x in spec.split(","))
+    st = torch.from_numpy(workloads.random_bytes(n * 200, seed=rank_seed(23, rank))).cuda().view(torch.int64)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        binding.keccak_p_batch(st, b, nr, n, stream)
+    ts = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        binding.keccak_p_batch(st, b, nr, n, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    return {"b": b, "nr": nr, "states": n, "ms": ms, "gstates_s": n / ms / 1e6, "hbm_gb_s": n * 400 / ms / 1e6}
 
 
 def measured_traffic():
