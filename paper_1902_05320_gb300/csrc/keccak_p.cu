@@ -79,53 +79,59 @@ __device__ __forceinline__ void small_round(uint32_t (&A)[25], int ir) {
     A[0] ^= L::load(uint32_t(c_rc255.v[ir]));
 }
 
-// States move between global memory and registers through shared memory: a
-// block copies its tile of kThreads consecutive 200-byte states with
-// coalesced 8-byte accesses (a warp touches 256 contiguous bytes per access),
-// and each thread then reads its own state from shared memory.  Two tile
-// buffers: the next tile's copies (cp.async, 8 bytes each) are issued before
-// the current tile is permuted, so a block's loads overlap its own
-// arithmetic.  Reading the states straight from global memory, each thread
-// 25 accesses 200 bytes apart, left the reduced-round runs waiting on memory.
-constexpr uint32_t kTileWords = kThreads * 25;                     // uint2 words of a tile (25.6 KB)
-constexpr size_t kTileSmem = 2 * size_t(kTileWords) * sizeof(uint2);  // two buffers
+// States move between global memory and registers through shared memory:
+// each warp takes tiles of 32 consecutive 200-byte states (6.4 KB), copied
+// with coalesced 8-byte accesses (the warp touches 256 contiguous bytes per
+// access), and each thread then reads its own state from shared memory.
+// Every warp has two tile buffers of its own: the next tile's copies
+// (cp.async, 8 bytes each) are issued before the current tile is permuted,
+// so a warp's loads overlap its own arithmetic, and warps synchronise only
+// among their own threads (tiles of 128 states per block, with block
+// barriers, measured 5-10% slower).  Reading the states straight from
+// global memory, each thread 25 accesses 200 bytes apart, left the
+// reduced-round runs waiting on memory.
+constexpr uint32_t kWarpTile = 32;                                   // states per warp tile
+constexpr uint32_t kTileWords = kWarpTile * 25;                      // uint2 words of a tile (6.4 KB)
+constexpr size_t kTileSmem = size_t(kThreads / 32) * 2 * kTileWords * sizeof(uint2);  // per block
 
-__device__ __forceinline__ void tile_load_async(uint32_t sdst, const uint64_t *states, uint64_t first, uint32_t cnt) {
-    const uint2 *src = reinterpret_cast<const uint2 *>(states + 25 * first);
-    for (uint32_t j = threadIdx.x; j < cnt * 25; j += kThreads)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sdst + 8 * j), "l"(src + j) : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-__device__ __forceinline__ void tile_out(const uint2 *sm, uint64_t *states, uint64_t first, uint32_t cnt) {
-    uint2 *dst = reinterpret_cast<uint2 *>(states + 25 * first);
-    for (uint32_t j = threadIdx.x; j < cnt * 25; j += kThreads) dst[j] = sm[j];
-}
-
-// The tiles of blockIdx.x, gridDim.x apart, each permuted state by state by
-// f(uint2 *state) in shared memory and written back in place.
+// The warp tiles of this warp, one warp-stride apart over the grid, each
+// permuted state by state by f(uint2 *state) in shared memory and written
+// back in place.
 template <class F>
 __device__ __forceinline__ void run_tiles(uint64_t *states, uint64_t n, uint2 *sm, F f) {
-    const uint64_t ntiles = (n + kThreads - 1) / kThreads;
-    const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(sm));
-    auto count = [&](uint64_t t) { return uint32_t(n - t * kThreads < kThreads ? n - t * kThreads : uint64_t(kThreads)); };
-    uint64_t tile = blockIdx.x;
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const uint64_t ntiles = (n + kWarpTile - 1) / kWarpTile;
+    const uint64_t nwarps = uint64_t(gridDim.x) * (blockDim.x / 32);
+    uint64_t tile = uint64_t(blockIdx.x) * (blockDim.x / 32) + wib;
+    uint2 *mine = sm + wib * 2 * kTileWords;
+    const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(mine));
+    auto count = [&](uint64_t t) {
+        return uint32_t(n - t * kWarpTile < kWarpTile ? n - t * kWarpTile : uint64_t(kWarpTile));
+    };
+    auto load = [&](uint32_t sdst, uint64_t t) {
+        const uint2 *src = reinterpret_cast<const uint2 *>(states + 25 * t * kWarpTile);
+        const uint32_t words = count(t) * 25;
+        for (uint32_t j = lane; j < words; j += 32)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sdst + 8 * j), "l"(src + j) : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     if (tile >= ntiles) return;
-    tile_load_async(sbase, states, tile * kThreads, count(tile));
-    for (uint32_t b = 0; tile < ntiles; tile += gridDim.x, b ^= 1u) {
-        const uint64_t next = tile + gridDim.x;
-        // The other buffer was last read before the barrier that ended the
-        // previous pass, so the next tile may be copied into it now.
-        if (next < ntiles) tile_load_async(sbase + (b ^ 1u) * kTileWords * 8u, states, next * kThreads, count(next));
+    load(sbase, tile);
+    for (uint32_t b = 0; tile < ntiles; tile += nwarps, b ^= 1u) {
+        const uint64_t next = tile + nwarps;
+        // The other buffer was last read before the warp barrier that ended
+        // the previous pass, so the next tile may be copied into it now.
+        if (next < ntiles) load(sbase + (b ^ 1u) * kTileWords * 8u, next);
         else asm volatile("cp.async.commit_group;" ::: "memory");  // an empty group keeps the count below uniform
         asm volatile("cp.async.wait_group 1;" ::: "memory");         // this tile's copies have landed
-        __syncthreads();
-        uint2 *cur = sm + b * kTileWords;
+        __syncwarp();
+        uint2 *cur = mine + b * kTileWords;
         const uint32_t cnt = count(tile);
-        if (threadIdx.x < cnt) f(cur + 25 * threadIdx.x);
-        __syncthreads();
-        tile_out(cur, states, tile * kThreads, cnt);
-        __syncthreads();
+        if (lane < cnt) f(cur + 25 * lane);
+        __syncwarp();
+        uint2 *dst = reinterpret_cast<uint2 *>(states + 25 * tile * kWarpTile);
+        for (uint32_t j = lane; j < cnt * 25; j += 32) dst[j] = cur[j];
+        __syncwarp();
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -260,8 +266,9 @@ int launch_keccak_p(uint64_t *states, int b, int nr, uint64_t n, cudaStream_t st
         case 4: return launch_small<16>(states, first_ir, nr, n, stream, dev);
         case 5: return launch_small<32>(states, first_ir, nr, n, stream, dev);
         default: {
-            // Staged through shared memory below 16 rounds (measured: 12
-            // rounds 2.53 -> 2.35 ms on 2^24 states; 24 rounds 3.84 -> 4.19 ms).
+            // Staged through shared memory below 16 rounds (measured on 2^24
+            // states: 12 rounds 2.53 ms read directly, 2.15 ms staged; 24
+            // rounds 3.84 ms directly, 4.02 ms staged).
             if (nr < 16) return launch_tiled(k_keccak_p_1600<true>, states, first_ir, nr, n, stream, dev);
             const uint64_t g =
                 persistent_grid(reinterpret_cast<const void *>(&k_keccak_p_1600<false>), kThreads, 0, n, dev);
