@@ -328,10 +328,13 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
     if (decided == KB_HOST_PATH_ZERO_COPY) return run_in_place(d_in, stride, len, variant, out_len, d_out, n, user, *dev);
     if (decided == KB_HOST_PATH_STAGED || n < kTrialMin)
         return run_staged(p, h_msgs, stride, len, variant, out_len, h_digests, n, user, *dev);
-    // Trial: a short warm-up of each path, then a quarter of the batch each,
-    // timed on the host (both paths are synchronous); the rest by the faster.
-    // Every message is hashed once, by one path or the other.
-    const uint64_t warm = std::max<uint64_t>(1, n / 64), quarter = n / 4;
+    // Trial: a short warm-up of each path, then two eighths of the batch each,
+    // alternating, timed on the host (both paths are synchronous); each path
+    // keeps the faster of its two timings, so that one call slowed by
+    // something outside it (a stall of the copy engines was seen to last
+    // tens of milliseconds) does not decide.  The rest of the batch goes by
+    // the faster path; every message is hashed once, by one path or the other.
+    const uint64_t warm = std::max<uint64_t>(1, n / 64), eighth = n / 8;
     uint64_t at = 0;
     auto staged = [&](uint64_t cnt) {
         const int rc = run_staged(p, h_msgs + at * stride, stride, len, variant, out_len, h_digests + at * out_len,
@@ -347,12 +350,16 @@ int keccak_batch_uniform_host(const uint8_t *h_msgs, uint64_t stride, uint64_t l
     };
     int rc = staged(warm);
     if (rc == KB_OK) rc = in_place(warm);
-    auto t = std::chrono::steady_clock::now();
-    if (rc == KB_OK) rc = staged(quarter);
-    const double t_staged = seconds_since(t);
-    t = std::chrono::steady_clock::now();
-    if (rc == KB_OK) rc = in_place(quarter);
-    const double t_in_place = seconds_since(t);
+    double t_staged = 1e30, t_in_place = 1e30;
+    for (int round = 0; round < 2 && rc == KB_OK; ++round) {
+        auto t = std::chrono::steady_clock::now();
+        rc = staged(eighth);
+        t_staged = std::min(t_staged, seconds_since(t));
+        if (rc != KB_OK) break;
+        t = std::chrono::steady_clock::now();
+        rc = in_place(eighth);
+        t_in_place = std::min(t_in_place, seconds_since(t));
+    }
     if (rc != KB_OK) return rc;
     const int choice = t_in_place < t_staged ? KB_HOST_PATH_ZERO_COPY : KB_HOST_PATH_STAGED;
     {

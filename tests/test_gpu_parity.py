@@ -293,10 +293,10 @@ def test_host_pipeline_matches_oracle(cuda_lib, oracle_mod, pinned, path):
 
 def test_host_path_trial_and_numa_buffers(cuda_lib, oracle_mod):
     # KB_HOST_PATH_AUTO on page-locked buffers from keccak_host_alloc: the first
-    # call of a size class hashes a warm-up and a quarter of the batch by each
-    # path, then the rest by the faster; every message must come out exactly
-    # once, across every boundary between the parts, and later calls use the
-    # decision.
+    # call of a size class hashes a warm-up by each path, then two eighths of
+    # the batch by each, alternating, then the rest by the faster; every
+    # message must come out exactly once, across every boundary between the
+    # parts, and later calls use the decision.
     cuda_lib.keccak_release()  # no earlier decision for this size class
     n, L = 700_000, 64
     assert cuda_lib.keccak_host_path_for(n) == cuda_lib.KB_HOST_PATH_AUTO
@@ -304,8 +304,8 @@ def test_host_path_trial_and_numa_buffers(cuda_lib, oracle_mod):
     h_in, h_out = cuda_lib.HostBuffer(n * L), cuda_lib.HostBuffer(n * 32)
     assert h_in.numa_node() >= -1 and h_out.numa_node() >= -1
     h_in.array[:] = msgs
-    warm, quarter = n // 64, n // 4
-    edges = [0, warm, 2 * warm, 2 * warm + quarter, 2 * warm + 2 * quarter, n]
+    warm, eighth = n // 64, n // 8
+    edges = [0, warm, 2 * warm] + [2 * warm + k * eighth for k in range(1, 5)] + [n]
     idx = np.unique(np.concatenate([np.arange(max(0, e - 3), min(n, e + 3)) for e in edges]
                                    + [np.random.default_rng(3).choice(n, 3000, replace=False)]))
     want = oracle_uniform(oracle_mod, msgs, L, L, 1, 32, n, idx)
