@@ -955,7 +955,7 @@ def measured_hbm_gbs() -> float:
 def serving_measurements(workloads, torch, rank, rate=200_000, seconds=10.0, with_oracle=False) -> dict:
     """The serving loop: Poisson arrivals at `rate` requests/s for `seconds`,
     messages log-uniform 32 B..1 MiB from a 4 GiB pinned pool, variants mixed,
-    admitted against a 2 GiB device budget, 32 batches in flight per lane."""
+    admitted against a 2 GiB device budget, 48 batches in flight per lane."""
     from paper_1902_05320_gb300.serve import Server
 
     from paper_1902_05320_gb300 import binding
@@ -971,10 +971,11 @@ def serving_measurements(workloads, torch, rank, rate=200_000, seconds=10.0, wit
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    # 32 batches in flight per lane: a long-lane stream stays busy until the
-    # slowest chain of its batch ends (16 per lane measured p99 31.7-108 ms
-    # where 32 gave 24.1-24.2 ms on the same box).
-    with Server(hbm_budget_bytes=2 << 30, max_inflight=32, max_batch_requests=4096) as srv:
+    # 48 batches in flight per lane: a long-lane stream stays busy until the
+    # slowest chain of its batch ends (measured p99: 16 per lane 31.7-108 ms,
+    # 32 per lane 24.1-24.2 ms with one run in seven at 35.9 ms, 48 per lane
+    # 23.6-23.7 ms in five runs out of five).
+    with Server(hbm_budget_bytes=2 << 30, max_inflight=48, max_batch_requests=4096) as srv:
         sampler.mark()
         st = srv.replay(pool, wl.offsets, wl.lens, wl.variants, wl.out_lens, wl.arrival_ns, outputs, lat)
         sampler.mark()

@@ -66,7 +66,7 @@ def _addr(x) -> int:
 class Server:
     """A continuous-batching hash server on the current device."""
 
-    def __init__(self, hbm_budget_bytes: int = 2 << 30, max_inflight: int = 32, max_batch_requests: int = 4096,
+    def __init__(self, hbm_budget_bytes: int = 2 << 30, max_inflight: int = 48, max_batch_requests: int = 4096,
                  max_batch_bytes: int = 256 << 20, long_threshold_perms: int = 0,
                  long_lane_parallel: bool = True):
         cfg = ServerConfig(hbm_budget_bytes, max_inflight, max_batch_requests, max_batch_bytes,

@@ -126,7 +126,7 @@ def test_full_size_serving_run_sampled(cuda_lib, oracle_mod):
     from paper_1902_05320_gb300.serve import Server
 
     wl = W.serving_workload(200_000, 10.0, seed=5, pool_bytes=4 << 30)
-    with Server(hbm_budget_bytes=2 << 30, max_inflight=32, max_batch_requests=4096) as srv:
+    with Server(hbm_budget_bytes=2 << 30, max_inflight=48, max_batch_requests=4096) as srv:
         got, lat, stats, _ = _replay(srv, torch, wl)
     assert stats["requests"] == wl.n and (lat > 0).all()
     pos = np.concatenate([[0], np.cumsum(wl.out_lens[:-1], dtype=np.uint64)])
