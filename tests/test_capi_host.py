@@ -139,3 +139,36 @@ def test_binding_signatures_cover_the_header():
     for name, nargs in protos.items():
         fn = getattr(lib, name)
         assert fn.argtypes is not None and len(fn.argtypes) == nargs, name
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # The ctypes mirrors of the header's structs (kb_queue_config,
+    # kb_server_config, kb_server_stats) must have the C compiler's size and
+    # field offsets, or the library would read and write the wrong bytes.
+    import shutil
+    import subprocess
+
+    from paper_1902_05320_gb300 import serve
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"kb_queue_config": binding.QueueConfig, "kb_server_config": serve.ServerConfig,
+               "kb_server_stats": serve.ServerStats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sha3gb.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = str(binding.HEADER).rsplit("/", 1)[0]
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
