@@ -455,7 +455,9 @@ def e2e_measurements(binding, torch, stream, msgs_np, digests, n_msgs, world, st
         except Exception as e:  # diagnostic only
             link[name] = f"probe failed: {e}"
     del probe_dev
-    reps = max(3, min(steps, 10))
+    # Up to 40 calls per path (~0.25 s each): one slow call then moves the mean
+    # by a few percent rather than by half.
+    reps = max(10, min(2 * steps, 40))
 
     per_call = {}
 
