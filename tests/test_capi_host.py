@@ -172,3 +172,28 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_readme_c_example_compiles(tmp_path):
+    # The C usage example in README.md compiles against the header and the
+    # CUDA runtime's header (warnings as errors), so the documented calls
+    # keep matching the ABI.
+    import os
+    import re
+    import shutil
+    import subprocess
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    blocks = re.findall(r"```c\n(.*?)```", open(os.path.join(root, "README.md")).read(), flags=re.S)
+    assert blocks, "README.md has no C example"
+    cuda_inc = next((d for d in ("/usr/local/cuda/include",) if os.path.exists(os.path.join(d, "cuda_runtime.h"))),
+                    None)
+    if cuda_inc is None or shutil.which("gcc") is None:
+        pytest.skip("no CUDA headers or C compiler")
+    for k, code in enumerate(blocks):
+        src = tmp_path / f"example{k}.c"
+        src.write_text(code)
+        r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"),
+                            "-I", cuda_inc, "-c", str(src), "-o", str(tmp_path / f"example{k}.o")],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
